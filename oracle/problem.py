@@ -1,0 +1,38 @@
+"""Build an oracle Problem and initial State from a synthetic workload description."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import system
+from .topology import build_topology
+
+
+def facet_inputs(cfg, topo, coords):
+    """Per-facet membrane model, leak conductances and stimulus mask, in facet order."""
+    n_f = len(topo.facets)
+    model = np.full(n_f, cfg.model, np.int32)
+    gleak = np.tile(np.asarray(cfg.g_leak, float), (n_f, 1))
+    if cfg.gK_sigma:
+        xi = cfg.elem_facet_xi()[topo.facet_elem_i, topo.facet_opp_i]
+        gleak[:, 1] = cfg.g_leak[1] * np.exp(cfg.gK_sigma * xi)
+    centroid_x = coords[topo.facets][:, :, 0].mean(axis=1)
+    mask = centroid_x < cfg.stim_xmax
+    return model, gleak, mask
+
+
+def from_config(cfg, dt=None):
+    m = cfg.mesh
+    p = cfg.params
+    topo = build_topology(m.coords, m.elems, m.elem_tag)
+    model, gleak, mask = facet_inputs(cfg, topo, m.coords)
+    pb = system.Problem(topo=topo, coords=m.coords, elems=m.elems, R=p["R"], T=p["T"], F=p["F"],
+                        Cm=p["Cm"], z=np.asarray(p["z"], float), D_i=np.asarray(p["D"], float),
+                        D_e=np.asarray(p["D"], float), dt=cfg.dt if dt is None else dt,
+                        facet_model=model, facet_gleak=gleak, gbar_Na=p["gbar_Na"],
+                        gbar_K=p["gbar_K"], phi_rest=p["phi_rest"], n_ode=25,
+                        stim_kind=cfg.stim_kind, stim_gbar=cfg.stim_gbar, stim_t0=cfg.stim_t0,
+                        stim_t1=cfg.stim_t1, stim_a=cfg.stim_a, stim_tau=cfg.stim_tau,
+                        stim_mask=mask)
+    system.discretize(pb)
+    s0 = system.initial_state(pb, p["c_i0"], p["c_e0"], p["phi_M0"], (p["n0"], p["m0"], p["h0"]))
+    return pb, s0

@@ -1,0 +1,109 @@
+"""Structured simplicial meshes shaped like the paper's Model A (Section 5.1).
+
+The unit square/cube is cut into N_x intervals per side. In 2D each square is
+split into two right triangles along its (0,0)-(1,1) diagonal; in 3D each cube
+is split into the six Kuhn (Freudenthal) tetrahedra that share the main
+diagonal, which gives a conforming tessellation. Vertex ids are lexicographic
+with x fastest. Cells are axis-aligned boxes whose faces are snapped to grid
+planes, so every element lies entirely inside one region.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class StructuredMesh:
+    dim: int
+    nx: int
+    coords: np.ndarray      # (n_vertices, dim) float64, metres
+    elems: np.ndarray       # (n_elems, dim+1) int32 vertex ids
+    elem_tag: np.ndarray    # (n_elems,) int32: 0 = extracellular, j>=1 = cell j
+    boxes: np.ndarray       # (n_cells, 2, dim) int64 snapped grid-index boxes [lo, hi]
+    length: float           # side of the domain in metres
+
+
+def _vid(idx, n1, dim):
+    v = idx[..., 0].astype(np.int64)
+    stride = n1
+    for a in range(1, dim):
+        v = v + idx[..., a].astype(np.int64) * stride
+        stride *= n1
+    return v
+
+
+def structured_mesh(dim: int, nx: int, length: float):
+    """Vertices and simplices of the uniform grid of [0, length]^dim."""
+    n1 = nx + 1
+    axes = [np.arange(n1, dtype=np.float64) / nx * length] * dim
+    grid = np.meshgrid(*axes, indexing="ij")
+    # lexicographic with x fastest
+    coords = np.stack([g.transpose(tuple(range(dim))[::-1]).reshape(-1) for g in grid], axis=1)
+    base = np.stack(np.meshgrid(*[np.arange(nx)] * dim, indexing="ij"), axis=-1)
+    base = base.transpose(tuple(range(dim))[::-1] + (dim,)).reshape(-1, dim)
+    elems = []
+    for perm in itertools.permutations(range(dim)):
+        if dim == 2 and perm not in ((0, 1), (1, 0)):
+            continue
+        path = [base.copy()]
+        cur = base.copy()
+        for ax in perm:
+            cur = cur.copy()
+            cur[:, ax] += 1
+            path.append(cur)
+        elems.append(np.stack([_vid(p, n1, dim) for p in path], axis=1))
+    # interleave so that the simplices of one grid box are consecutive
+    elems = np.stack(elems, axis=1).reshape(-1, dim + 1).astype(np.int32)
+    return coords, elems
+
+
+def snap_boxes(lo: np.ndarray, hi: np.ndarray, nx: int) -> np.ndarray:
+    """Snap box corners (fractions of the side) to grid planes, half away from zero."""
+    lo_i = np.floor(np.asarray(lo) * nx + 0.5).astype(np.int64)
+    hi_i = np.floor(np.asarray(hi) * nx + 0.5).astype(np.int64)
+    return np.stack([lo_i, hi_i], axis=-2)
+
+
+def box_cells(n_per_side: int, side: float, gap: float, dim: int, jitter=None, rng=None):
+    """Centred n^dim array of cubic cells with the given side and gap (fractions of the domain).
+
+    With ``jitter`` = (a, b), each side of each cell is scaled about the cell centre by
+    an independent U(a, b) factor drawn from ``rng``.
+    """
+    extent = n_per_side * side + (n_per_side - 1) * gap
+    start = 0.5 - extent / 2
+    lows, highs = [], []
+    for idx in itertools.product(range(n_per_side), repeat=dim):
+        lo = np.array([start + i * (side + gap) for i in idx[::-1]])
+        hi = lo + side
+        if jitter is not None:
+            c = 0.5 * (lo + hi)
+            s = rng.uniform(jitter[0], jitter[1], size=dim) * side
+            lo, hi = c - s / 2, c + s / 2
+        lows.append(lo)
+        highs.append(hi)
+    return np.array(lows), np.array(highs)
+
+
+def tag_elements(coords_idx_centroid: np.ndarray, boxes: np.ndarray) -> np.ndarray:
+    """Tag each element by the snapped box that contains its centroid (grid units)."""
+    tag = np.zeros(coords_idx_centroid.shape[0], dtype=np.int32)
+    for j, (lo, hi) in enumerate(boxes):
+        inside = np.all((coords_idx_centroid > lo) & (coords_idx_centroid < hi), axis=1)
+        tag[inside] = j + 1
+    return tag
+
+
+def make_mesh(dim: int, nx: int, length: float, lo, hi) -> StructuredMesh:
+    coords, elems = structured_mesh(dim, nx, length)
+    boxes = snap_boxes(np.atleast_2d(lo), np.atleast_2d(hi), nx)
+    if np.any(boxes[:, 1] - boxes[:, 0] < 1):
+        raise ValueError("a cell snapped to zero width")
+    if np.any(boxes[:, 0] < 1) or np.any(boxes[:, 1] > nx - 1):
+        raise ValueError("cells must stay inside the domain interior")
+    centroid = coords[elems].mean(axis=1) / length * nx
+    tag = tag_elements(centroid, boxes)
+    return StructuredMesh(dim, nx, coords, elems, tag, boxes, length)
