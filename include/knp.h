@@ -1,0 +1,228 @@
+/*
+ * knp.h - C ABI of the GB300 KNP-EMI step library (libknp.so).
+ *
+ * The library advances the KNP-EMI equations (ion concentrations [k]_r and
+ * potentials phi_r in the intracellular (i) and extracellular (e) regions,
+ * coupled across the membrane Gamma) with the implicit-explicit linearised
+ * time step of Section 3.2 of Benedusi, Ellingsrud, Herlyng and Rognes,
+ * "Scalable approximation and solvers for ionic electrodiffusion in cellular
+ * geometries" (arXiv 2403.04491). Each step is: membrane update (Section 3.2),
+ * assembly of A_{n-1} and f_n (Section 4.1, Eq. 4.2), and the solve of
+ * A_{n-1} u_n = f_n by flexible GMRES(30) right-preconditioned with one
+ * algebraic-multigrid V-cycle on the block-diagonal P_0 (Eq. 4.3, Section 4.2,
+ * Section 6.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns knp_status; knp_last_error() gives a
+ *    thread-local, human-readable message for the last failure.
+ *    No C++ exception crosses this boundary.
+ *  - Inputs are caller-owned and copied at create time. Handles are
+ *    library-owned and freed by their *_destroy function.
+ *  - Device work is enqueued on the CUDA stream given at problem creation
+ *    (a cudaStream_t passed as void*; NULL = legacy default stream). Calls
+ *    that return host data synchronise that stream first.
+ *  - One handle is not thread-safe; separate handles are independent.
+ *  - Units are SI: m, s, V, mol/m^3, S/m^2, F/m^2.
+ *  - Region node order is increasing vertex id; the membrane facet order is
+ *    lexicographic in the facet's sorted vertex ids (see knp_mesh_facets).
+ */
+#ifndef KNP_H
+#define KNP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t knp_status;
+#define KNP_OK                 0
+#define KNP_ERR_INVALID_ARG    1  /* a NULL pointer, a size out of range, an inconsistent option */
+#define KNP_ERR_INVALID_MESH   2  /* degenerate element, cells sharing a facet or a vertex, a cell without membrane */
+#define KNP_ERR_OOM            3  /* host or device allocation failed */
+#define KNP_ERR_CUDA           4  /* a CUDA runtime call failed (message has the CUDA error string) */
+#define KNP_ERR_NOT_CONVERGED  5  /* GMRES reached max_it without meeting rtol; the iterate is kept */
+#define KNP_ERR_NUMERIC        6  /* NaN/Inf in a residual, a non-positive diagonal, a singular coarse matrix */
+#define KNP_ERR_STATE          7  /* call out of order (e.g. knp_solve before knp_assemble_step) */
+
+typedef enum { KNP_HOST = 0, KNP_DEVICE = 1 } knp_memspace;
+typedef enum { KNP_MODEL_LEAK = 0, KNP_MODEL_HH = 1 } knp_membrane_model;
+typedef enum { KNP_STIM_NONE = 0, KNP_STIM_WINDOW = 1, KNP_STIM_PERIODIC_EXP = 2 } knp_stimulus_kind;
+typedef enum { KNP_PREC_FP64 = 0, KNP_PREC_FP32 = 1 } knp_precision;
+
+#define KNP_MAX_IONS 4
+
+typedef struct knp_mesh knp_mesh;
+typedef struct knp_problem knp_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Mesh (Section 3.3: conforming simplicial T = T_i U T_e matched at Gamma)   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t dim;               /* 2 (triangles) or 3 (tetrahedra) */
+    int64_t n_vertices;
+    const double* coords;      /* host [n_vertices * dim], metres, row-major */
+    int64_t n_elems;
+    const int32_t* elems;      /* host [n_elems * (dim+1)] vertex ids */
+    const int32_t* elem_tag;   /* host [n_elems]: 0 = extracellular, j >= 1 = cell j */
+} knp_mesh_desc;
+
+typedef struct {
+    int32_t dim;
+    int64_t n_vertices, n_elems;
+    int64_t N_i, N_e;            /* region node counts (membrane vertices counted in both) */
+    int64_t n_facets;            /* membrane facets */
+    int64_t n_membrane_vertices;
+    int32_t n_cells;             /* largest cell tag */
+    int64_t pin_vertex;          /* extracellular vertex of the point pin (Remark 4.1) */
+    int64_t n_dof;               /* (N_i + N_e)(n_ions + 1) for n_ions = 3 */
+} knp_mesh_info;
+
+/* Builds the topology: membrane facets are the facets shared by an element of
+ * tag 0 and one of tag >= 1; every membrane vertex gets one node in each
+ * region (Section 3.3; the count of Section 5.1). The pin is the extracellular
+ * vertex nearest to the origin, ties broken by lowest id (Remark 4.1).
+ * Errors: KNP_ERR_INVALID_ARG (NULL, dim not 2/3, ids out of range),
+ * KNP_ERR_INVALID_MESH (zero-volume element, two cells sharing a facet or a
+ * vertex, regions touching outside membrane facets, a cell with no facet). */
+knp_status knp_mesh_create(const knp_mesh_desc* desc, knp_mesh** out);
+knp_status knp_mesh_get_info(const knp_mesh* mesh, knp_mesh_info* info);
+/* Region node -> vertex id: nodes_i[N_i], nodes_e[N_e] (host, caller-allocated; either may be NULL). */
+knp_status knp_mesh_nodes(const knp_mesh* mesh, int32_t* nodes_i, int32_t* nodes_e);
+/* Membrane facets in library order (host, caller-allocated, any may be NULL):
+ * vertices[n_facets*dim] sorted vertex ids; elem_i[n_facets] intracellular
+ * element; opp_i[n_facets] local index (0..dim) of elem_i's vertex opposite
+ * the facet; cell[n_facets] cell tag. */
+knp_status knp_mesh_facets(const knp_mesh* mesh, int32_t* vertices, int32_t* elem_i,
+                           int32_t* opp_i, int32_t* cell);
+void knp_mesh_destroy(knp_mesh* mesh);
+
+/* ------------------------------------------------------------------------- */
+/* Problem (Sections 2, 3.2, Table 2)                                        */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t n_ions;                  /* |K|, 1..KNP_MAX_IONS */
+    double z[KNP_MAX_IONS];          /* valences z_k */
+    double D_i[KNP_MAX_IONS];        /* D_i^k, m^2/s */
+    double D_e[KNP_MAX_IONS];        /* D_e^k, m^2/s */
+    double R, T, F;                  /* gas constant, temperature, Faraday constant (psi = RT/F) */
+    double Cm;                       /* membrane capacitance, F/m^2 */
+    double dt;                       /* time step, s */
+    double c_i0[KNP_MAX_IONS];       /* uniform initial [k]_i^0 */
+    double c_e0[KNP_MAX_IONS];       /* uniform initial [k]_e^0 */
+    double phi_M0;                   /* initial membrane potential; phi_i^0 = phi_M0, phi_e^0 = 0 */
+    /* membrane (Eq. 2.9 and the leak model): per facet, in knp_mesh_facets order */
+    const int32_t* facet_model;      /* host [n_facets]: KNP_MODEL_LEAK or KNP_MODEL_HH */
+    const double* facet_gleak;       /* host [n_facets * n_ions] leak conductances g_leak^k */
+    int32_t ion_na, ion_k;           /* ions carrying the HH Na / K channels and the stimulus (Na) */
+    double gbar_na, gbar_k;          /* HH maximal conductances on HH facets */
+    double phi_rest;                 /* HH resting potential, V */
+    double w0[3];                    /* initial gates (n, m, h) */
+    int32_t n_ode;                   /* Rush-Larsen substeps per step (25 in Section 6.2) */
+    /* stimulus g_stim^Na(t) on masked facets, evaluated at t_{n-1} */
+    int32_t stim_kind;               /* knp_stimulus_kind */
+    double stim_gbar, stim_t0, stim_t1, stim_a, stim_tau;
+    const uint8_t* stim_mask;        /* host [n_facets] (1 = stimulated) or NULL = all facets */
+} knp_problem_desc;
+
+/* Creates device state for one simulation on `stream`; u_0 as in Section 2.3
+ * with phi_i^0 = phi_M0 and phi_e^0 = 0, gates w_0 at every membrane vertex.
+ * Errors: KNP_ERR_INVALID_ARG, KNP_ERR_OOM, KNP_ERR_CUDA. */
+knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc, void* stream,
+                              knp_problem** out);
+void knp_problem_destroy(knp_problem* prob);
+
+/* Membrane update and assembly for the current step n (Section 3.2, Section
+ * 4.1): from u_{n-1}, w_{n-1} and t_{n-1}, computes w_n by Rush-Larsen with
+ * phi_M frozen, the explicit I_ch^{k,n-1}, alpha^{n-1}, C^{n-1}, the values of
+ * A_{n-1} in its fixed pattern and f_n (Eq. 4.2), with the point pin of
+ * Remark 4.1. Stream-ordered; returns without synchronising. */
+knp_status knp_assemble_step(knp_problem* prob);
+
+typedef struct {
+    int32_t precision;          /* knp_precision of the hierarchy and V-cycle (FGMRES stays FP64) */
+    double theta;               /* strength threshold of the aggregation graph (0.08 default) */
+    int32_t coarse_max;         /* stop coarsening at <= this many nodes (dense coarse solve) */
+    int32_t max_levels;
+    int32_t cheb_degree;        /* Chebyshev smoothing degree (pre and post) */
+    double cheb_ratio;          /* lower eigenvalue bound = lambda_max / cheb_ratio */
+} knp_amg_opts;
+
+/* Smoothed-aggregation AMG on P_0 (Eq. 4.3) assembled from the initial
+ * state and reused for every step (Section 4.2). Must follow
+ * knp_problem_create and precede knp_solve. Errors: KNP_ERR_INVALID_ARG,
+ * KNP_ERR_OOM, KNP_ERR_NUMERIC (singular coarse matrix), KNP_ERR_CUDA. */
+knp_status knp_amg_setup(knp_problem* prob, const knp_amg_opts* opts);
+
+typedef struct {
+    double rtol;       /* on the preconditioned residual: ||S M^-1 r||_g <= rtol ||S u_{n-1}||_g for the
+                          concentration part and the potential part g, S^2 = diag(P_0), M^-1 = one
+                          V-cycle on P_0 (the paper's preconditioned test, Section 6.2, in the scaled
+                          norm and relative to the initial guess) */
+    int32_t restart;   /* 30 (Section 6.2) */
+    int32_t max_it;    /* total iterations */
+} knp_solve_opts;
+
+typedef struct {
+    int32_t iterations;
+    int32_t restarts;
+    double true_relres;    /* scaled true residual ||S^-1 (f - A u)|| / ||S^-1 f|| at exit */
+    double ms;             /* wall time of the solve (host clock, includes synchronisation) */
+} knp_solve_stats;
+
+/* FGMRES(restart), FP64, x_0 = u_{n-1} (Section 6.2), right-preconditioned by
+ * one V-cycle on P_0. On success the step is committed: the state becomes
+ * (u_n, w_n) and t advances by dt. KNP_ERR_NOT_CONVERGED keeps the last
+ * iterate in u and does not advance w or t. */
+knp_status knp_solve(knp_problem* prob, const knp_solve_opts* opts, knp_solve_stats* stats);
+
+typedef struct {
+    int32_t iterations;
+    double true_relres;
+} knp_step_stats;
+
+/* nsteps x (knp_assemble_step, knp_solve, t += dt). per_step may be NULL. */
+knp_status knp_step(knp_problem* prob, int32_t nsteps, const knp_solve_opts* opts,
+                    knp_step_stats* per_step);
+
+/* State access in region node order. Buffers are [n_ions * N_r] (ion-major)
+ * for concentrations, [N_r] for potentials, [3 * n_membrane_vertices] (gate-
+ * major n, m, h) for gates; any pointer may be NULL. `space` says where the
+ * caller's buffers live. knp_state_get synchronises the stream. */
+knp_status knp_state_get(const knp_problem* prob, knp_memspace space, double* c_i, double* phi_i,
+                         double* c_e, double* phi_e, double* gates, double* t);
+knp_status knp_state_set(knp_problem* prob, knp_memspace space, const double* c_i, const double* phi_i,
+                         const double* c_e, const double* phi_e, const double* gates, double t);
+
+/* ------------------------------------------------------------------------- */
+/* Inspection entry points (for parity tests against an independent          */
+/* implementation; not needed to run a simulation)                            */
+/* ------------------------------------------------------------------------- */
+
+/* Unknown order used by the inspection calls: the paper's Eq. 4.2 order
+ * [c_i^1..c_i^K, phi_i, c_e^1..c_e^K, phi_e], each block in region node order;
+ * n = n_dof. */
+
+/* f_n of the last knp_assemble_step into rhs[n] (host). */
+knp_status knp_rhs_get(const knp_problem* prob, double* rhs);
+/* y = A_{n-1} x with the last assembled operator; x, y host [n]. */
+knp_status knp_apply_operator(knp_problem* prob, const double* x, double* y);
+/* Entries of A_{n-1}: for each (row, col) pair in the Eq. 4.2 order, the value
+ * (0 where the entry is outside the pattern). rows, cols, vals host [count]. */
+knp_status knp_operator_entries(knp_problem* prob, int64_t count, const int64_t* rows,
+                                const int64_t* cols, double* vals);
+/* z = V-cycle(P_0) r (one application of the preconditioner, unscaled); host [n]. */
+knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* z);
+/* Hierarchy summary: levels, per-level node counts and nonzeros (host arrays of
+ * length >= max_levels), operator complexity. */
+knp_status knp_amg_info(const knp_problem* prob, int32_t* levels, int64_t* nodes, int64_t* nnz,
+                        double* op_complexity);
+
+const char* knp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KNP_H */

@@ -1,0 +1,70 @@
+// Internal declarations shared by the translation units of libknp.so.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/knp.h"
+
+namespace knp {
+
+// Thread-local error message behind knp_last_error().
+void set_error(const std::string& msg);
+
+struct Error {
+    knp_status code;
+    std::string msg;
+};
+
+#define KNP_FAIL(code, ...)                                   \
+    do {                                                      \
+        char _buf[512];                                       \
+        std::snprintf(_buf, sizeof(_buf), __VA_ARGS__);       \
+        throw ::knp::Error{(code), std::string(_buf)};        \
+    } while (0)
+
+#define KNP_REQUIRE(cond, code, ...) \
+    do {                             \
+        if (!(cond)) KNP_FAIL(code, __VA_ARGS__); \
+    } while (0)
+
+// Runs f, converting exceptions into a status and a message.
+template <class F>
+knp_status guarded(F&& f) {
+    try {
+        f();
+        return KNP_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return KNP_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_error(e.what());
+        return KNP_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace knp
+
+// Topology of a conforming mesh with duplicated membrane nodes (Section 3.3).
+struct knp_mesh {
+    int32_t dim = 0;
+    int64_t nv = 0, ne = 0;
+    std::vector<double> coords;       // [nv*dim]
+    std::vector<int32_t> elems;       // [ne*(dim+1)]
+    std::vector<int32_t> tag;         // [ne]
+    std::vector<int32_t> nodes_i, nodes_e;   // region node -> vertex (increasing)
+    std::vector<int32_t> loc_i, loc_e;       // vertex -> region node, -1 if absent
+    std::vector<int32_t> elems_i, elems_e;   // element ids per region
+    std::vector<int32_t> facets;             // [nf*dim] sorted vertex ids, lexicographic
+    std::vector<int32_t> facet_elem_i, facet_opp_i, facet_cell;
+    std::vector<int32_t> mverts;             // membrane vertices, increasing
+    std::vector<int32_t> node_cell_i;        // cell tag of each intracellular node
+    int64_t pin_vertex = -1;
+    int32_t n_cells = 0;
+    int64_t nf() const { return (int64_t)facet_cell.size(); }
+};

@@ -1,0 +1,363 @@
+// Flexible GMRES(m), FP64, right-preconditioned by one V-cycle on P_0 (Section 4.2,
+// Section 6.2: restart 30, x_0 = u_{n-1}).
+//
+// The Krylov space is built for the symmetrically scaled system
+// S^-1 A S^-1 (S x) = S^-1 f with S^2 = diag(P_0), which evens out the concentration and
+// potential rows (their magnitudes differ by orders of magnitude); the scaling is applied
+// on the fly (SpMV row scale, V-cycle input scale), so the preconditioned directions
+// z_j live in the unscaled solution space and x = x_0 + Z y directly. Orthogonalisation
+// is classical Gram-Schmidt with one reorthogonalisation (CGS2) in three fused passes.
+//
+// Stopping test: the preconditioned residual, as in Section 6.2, measured in the scaled
+// norm and relative to the initial guess, for the concentrations and the potentials apart:
+// ||S M^-1 r_k||_g <= rtol ||S x_0||_g for g in {c, phi}. A residual norm
+// alone is blind to the per-cell constant of phi_i (the intracellular potential block is
+// singular up to the small membrane mass), while M^-1 r approximates the error. For the
+// FGMRES iterate, M^-1 r_k = Z_{k+1} c with c = Q_k^T g_k e_{k+1} from the Givens rotations,
+// so its S-norms follow from the S^2-weighted Gram matrices of Z, one row per iteration.
+// (Apart, because the scaled concentrations outweigh the scaled potentials by two orders.)
+// The host sees one Hessenberg column and one Gram row per iteration.
+#include <chrono>
+#include <cmath>
+
+#include "gmres.h"
+#include "problem.h"
+#include "vcycle.h"
+
+namespace knp {
+
+namespace {
+
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int MAXV = 32;          // restart + 2
+constexpr int MAXW = 2 * MAXV;    // partial-sum slots per block
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double* __restrict__ partial) {
+    __shared__ double sh[RED_THREADS / 32][NV];
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    for (int k = 0; k < nv; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double s = 0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+        partial[(int64_t)blockIdx.x * MAXW + threadIdx.x] = s;
+    }
+}
+
+// partial[b][k] = block b's share of <V_k, w>_s for k < nv, and of <w, w>_s at k = nv, where
+// <a, b>_s = sum_i s_i^2 a_i b_i (s = NULL: plain dot)
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n4, const double* __restrict__ V, int64_t ldv, int nv,
+                                                      const double* __restrict__ w, const double* __restrict__ s,
+                                                      double* __restrict__ partial) {
+    double acc[MAXV];
+    for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        if (s) wi *= s[i] * s[i];
+        for (int k = 0; k < nv; ++k) acc[k] += V[k * ldv + i] * wi;
+        acc[nv] += wi * w[i];
+    }
+    block_reduce_store<MAXV>(acc, nv + 1, partial);
+}
+
+// S^2-weighted dots split by field group: slot 2k holds the concentration part (fields 0..2) of
+// <V_k, w>_S and slot 2k+1 the potential part (field 3); slots 2nv, 2nv+1 hold <w, w>_S.
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_split(int64_t n4, const double* __restrict__ V, int64_t ldv,
+                                                            int nv, const double* __restrict__ w,
+                                                            const double* __restrict__ s,
+                                                            double* __restrict__ partial) {
+    double acc[MAXW];
+    for (int k = 0; k < MAXW; ++k) acc[k] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const int grp = (i & 3) == 3;
+        double wi = w[i] * s[i] * s[i];
+        for (int k = 0; k < nv; ++k) acc[2 * k + grp] += V[k * ldv + i] * wi;
+        acc[2 * nv + grp] += wi * w[i];
+    }
+    block_reduce_store<MAXW>(acc, 2 * nv + 2, partial);
+}
+
+// w' = w - sum_k h[k] V_k (in place); partial sums of <V_k, w'> and <w', w'>
+__global__ void __launch_bounds__(RED_THREADS) k_orth_update_dot(int64_t n4, const double* __restrict__ V, int64_t ldv,
+                                                                 int nv, const double* __restrict__ h,
+                                                                 double* __restrict__ w, double* __restrict__ partial) {
+    double acc[MAXV];
+    for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
+    __shared__ double hs[MAXV];
+    if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        double vk[MAXV];
+        double wi = w[i];
+        for (int k = 0; k < nv; ++k) {
+            vk[k] = V[k * ldv + i];
+            wi -= hs[k] * vk[k];
+        }
+        w[i] = wi;
+        for (int k = 0; k < nv; ++k) acc[k] += vk[k] * wi;
+        acc[nv] += wi * wi;
+    }
+    block_reduce_store<MAXV>(acc, nv + 1, partial);
+}
+
+// out[k] = sum_b partial[b][k]
+__global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nv, double* __restrict__ out) {
+    int k = blockIdx.x;
+    if (k >= nv) return;
+    double s = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)b * MAXW + k];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = sh[0];
+}
+
+// v_out = (w - sum_k h2[k] V_k) / eta, eta^2 = <w,w> - |h2|^2 (w = v_out in place)
+__global__ void k_orth_final(int64_t n4, const double* __restrict__ V, int64_t ldv, int nv,
+                             const double* __restrict__ h2, double* __restrict__ w) {
+    __shared__ double hs[MAXV];
+    __shared__ double inv_eta;
+    if (threadIdx.x < nv) hs[threadIdx.x] = h2[threadIdx.x];
+    if (threadIdx.x == 0) {
+        double s = h2[nv];
+        for (int k = 0; k < nv; ++k) s -= h2[k] * h2[k];
+        inv_eta = s > 0 ? 1.0 / sqrt(s) : 0.0;
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        for (int k = 0; k < nv; ++k) wi -= hs[k] * V[k * ldv + i];
+        w[i] = wi * inv_eta;
+    }
+}
+
+// x += sum_k y[k] Z_k
+__global__ void k_update_x(int64_t n4, const double* __restrict__ Z, int64_t ldz, int nz, const double* __restrict__ y,
+                           double* __restrict__ x) {
+    __shared__ double ys[MAXV];
+    if (threadIdx.x < nz) ys[threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = x[i];
+        for (int k = 0; k < nz; ++k) s += ys[k] * Z[k * ldz + i];
+        x[i] = s;
+    }
+}
+
+__global__ void k_scale_copy(int64_t n4, const double* __restrict__ a, const double* __restrict__ s,
+                             double* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n4) out[i] = a[i] * s[i];
+}
+
+__global__ void k_scale_inplace(int64_t n4, double* __restrict__ v, double s) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n4) v[i] *= s;
+}
+
+}  // namespace
+
+struct GmresWork {
+    int restart = 0;
+    int64_t n4 = 0;
+    DArray<double> V, Z, partial, dots, y, tmp;
+    std::vector<double> hh;
+};
+
+GmresWork* gmres_work(knp_problem* p, int restart) {
+    if (p->gw && p->gw->restart == restart) return p->gw;
+    delete p->gw;
+    p->gw = nullptr;
+    auto* g = new GmresWork();
+    g->restart = restart;
+    g->n4 = 4 * p->n_nodes;
+    g->V.alloc((restart + 1) * g->n4);
+    g->Z.alloc((restart + 1) * g->n4);
+    g->partial.alloc(RED_BLOCKS * MAXW);
+    g->dots.alloc(2 * MAXV + MAXW);
+    g->y.alloc(MAXV);
+    g->tmp.alloc(g->n4);
+    g->hh.resize(2 * MAXV + MAXW);
+    p->gw = g;
+    return g;
+}
+
+void gmres_free(GmresWork* g) { delete g; }
+
+// squared norm of a device vector (through the multi-dot kernels)
+static double norm2_dev(GmresWork& g, const double* v, cudaStream_t st) {
+    k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(g.n4, nullptr, 0, 0, v, nullptr, g.partial.p);
+    k_reduce<<<1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 1, g.dots.p);
+    double s;
+    KNP_CUDA(cudaMemcpyAsync(&s, g.dots.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KNP_CUDA(cudaStreamSynchronize(st));
+    return s;
+}
+
+knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stats& stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int m = o.restart;
+    KNP_REQUIRE(m >= 1 && m + 2 <= MAXV, KNP_ERR_INVALID_ARG, "restart must be in [1, %d]", MAXV - 2);
+    GmresWork& g = *gmres_work(p, m);
+    cudaStream_t st = p->stream;
+    const int64_t n4 = g.n4;
+    const unsigned nb = (unsigned)((n4 + 255) / 256);
+    double* x = p->u.p;
+    // reference norms ||S x_0|| of the stopping test, concentrations and potentials apart
+    k_mdot_split<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, 0, x, p->svec.p, g.partial.p);
+    k_reduce<<<2, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2, g.dots.p + 2 * MAXV);
+    double xn2[2];
+    KNP_CUDA(cudaMemcpyAsync(xn2, g.dots.p + 2 * MAXV, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KNP_CUDA(cudaStreamSynchronize(st));
+    KNP_REQUIRE(std::isfinite(xn2[0]) && std::isfinite(xn2[1]), KNP_ERR_NUMERIC, "initial guess is not finite");
+    k_scale_copy<<<nb, 256, 0, st>>>(n4, p->f.p, p->sinv.p, g.tmp.p);
+    const double bnorm = std::sqrt(norm2_dev(g, g.tmp.p, st));
+    KNP_REQUIRE(std::isfinite(bnorm), KNP_ERR_NUMERIC, "right-hand side is not finite");
+    knp_status_detail res{KNP_OK, 0, 0, 0.0};
+    double tol[2];
+    for (int q = 0; q < 2; ++q) tol[q] = o.rtol * (xn2[q] > 0 ? std::sqrt(xn2[q]) : 1.0);
+    const int m1 = m + 1;
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), G(2 * m1 * m1);
+    int its = 0, restarts = 0;
+    bool converged = false;
+    double beta = 0;
+    while (!converged) {
+        // V_0 = S^-1 (f - A x)
+        op_apply(p, x, g.V.p, p->sinv.p, p->f.p);
+        beta = std::sqrt(norm2_dev(g, g.V.p, st));
+        KNP_REQUIRE(std::isfinite(beta), KNP_ERR_NUMERIC, "residual is not finite");
+        if (beta == 0.0) {
+            converged = true;
+            break;
+        }
+        if (its >= o.max_it) break;
+        if (its > 0) restarts++;
+        k_scale_inplace<<<nb, 256, 0, st>>>(n4, g.V.p, 1.0 / beta);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int k_done = 0;   // Arnoldi steps whose Hessenberg columns are kept
+        for (int j = 0; j <= m; ++j) {
+            double* vj = g.V.p + (int64_t)j * n4;
+            double* zj = g.Z.p + (int64_t)j * n4;
+            // z_j = V-cycle(S v_j); row j of the S^2-weighted Gram matrices of Z (two field groups)
+            vcycle_apply(p, vj, p->svec.p, zj);
+            k_mdot_split<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.Z.p, n4, j, zj, p->svec.p, g.partial.p);
+            k_reduce<<<2 * j + 2, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2 * j + 2, g.dots.p + 2 * MAXV);
+            const bool arnoldi = (j < m) && (its < o.max_it);
+            int nv = j + 1;
+            if (arnoldi) {
+                double* w = g.V.p + (int64_t)(j + 1) * n4;
+                op_apply(p, zj, w, p->sinv.p, nullptr);
+                k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, w, nullptr, g.partial.p);
+                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p);
+                k_orth_update_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, g.dots.p, w, g.partial.p);
+                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p + MAXV);
+                k_orth_final<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, g.dots.p + MAXV, w);
+            }
+            KNP_CUDA(cudaMemcpyAsync(g.hh.data(), g.dots.p, (2 * MAXV + MAXW) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+            KNP_CUDA(cudaStreamSynchronize(st));
+            KNP_CUDA(cudaGetLastError());
+            for (int q = 0; q < 2; ++q)
+                for (int a = 0; a <= j; ++a)
+                    G[q * m1 * m1 + j * m1 + a] = G[q * m1 * m1 + a * m1 + j] = g.hh[2 * MAXV + 2 * a + q];
+            // preconditioned residual of the iterate after k_done = j steps: M^-1 r = Z c with
+            // c = Q^T (0, .., 0, g_j); its S-norm is sqrt(c^T G c)
+            {
+                const int k = j;
+                std::vector<double> c(k + 1, 0.0);
+                c[k] = gv[k];
+                for (int i = k - 1; i >= 0; --i) {
+                    double a = c[i], b = c[i + 1];
+                    c[i] = cs[i] * a - sn[i] * b;
+                    c[i + 1] = sn[i] * a + cs[i] * b;
+                }
+                bool ok = true;
+                for (int q = 0; q < 2; ++q) {
+                    double est2 = 0;
+                    for (int a = 0; a <= k; ++a)
+                        for (int b = 0; b <= k; ++b) est2 += c[a] * c[b] * G[q * m1 * m1 + a * m1 + b];
+                    KNP_REQUIRE(std::isfinite(est2), KNP_ERR_NUMERIC, "preconditioned residual is not finite");
+                    ok &= std::sqrt(std::max(est2, 0.0)) <= tol[q];
+                }
+                if (ok) {
+                    converged = true;
+                    k_done = j;
+                    break;
+                }
+            }
+            if (!arnoldi) {
+                k_done = j;
+                break;
+            }
+            double s2 = g.hh[MAXV + nv];
+            double eta2 = s2;
+            for (int k = 0; k < nv; ++k) {
+                H[k * m + j] = g.hh[k] + g.hh[MAXV + k];
+                eta2 -= g.hh[MAXV + k] * g.hh[MAXV + k];
+            }
+            KNP_REQUIRE(std::isfinite(eta2), KNP_ERR_NUMERIC, "Arnoldi vector is not finite");
+            double eta = eta2 > 0 ? std::sqrt(eta2) : 0.0;
+            H[(j + 1) * m + j] = eta;
+            for (int k = 0; k < j; ++k) {
+                double a = H[k * m + j], b = H[(k + 1) * m + j];
+                H[k * m + j] = cs[k] * a + sn[k] * b;
+                H[(k + 1) * m + j] = -sn[k] * a + cs[k] * b;
+            }
+            double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+            cs[j] = H[j * m + j] / den;
+            sn[j] = H[(j + 1) * m + j] / den;
+            H[j * m + j] = den;
+            H[(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            its++;
+            k_done = j + 1;
+            if (eta == 0.0) {
+                converged = true;   // happy breakdown: the Krylov space holds the solution
+                break;
+            }
+        }
+        if (k_done > 0) {
+            // y = R^-1 g (upper triangular), x += Z y
+            std::vector<double> y(k_done);
+            for (int k = k_done - 1; k >= 0; --k) {
+                double s = gv[k];
+                for (int q = k + 1; q < k_done; ++q) s -= H[k * m + q] * y[q];
+                y[k] = s / H[k * m + k];
+            }
+            KNP_CUDA(cudaMemcpyAsync(g.y.p, y.data(), k_done * sizeof(double), cudaMemcpyHostToDevice, st));
+            k_update_x<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.Z.p, n4, k_done, g.y.p, x);
+            KNP_CUDA(cudaGetLastError());
+        }
+        if (!converged && its >= o.max_it) {
+            res.code = KNP_ERR_NOT_CONVERGED;
+            break;
+        }
+    }
+    // report the scaled true residual of the final iterate
+    op_apply(p, x, g.tmp.p, p->sinv.p, p->f.p);
+    double rn = std::sqrt(norm2_dev(g, g.tmp.p, st));
+    double relres = bnorm > 0 ? rn / bnorm : 0.0;
+    if (!converged) res.code = KNP_ERR_NOT_CONVERGED;
+    res.iterations = its;
+    res.restarts = restarts;
+    res.relres = relres;
+    stats.iterations = its;
+    stats.restarts = restarts;
+    stats.true_relres = relres;
+    stats.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return res;
+}
+
+}  // namespace knp

@@ -1,0 +1,472 @@
+// Problem creation: node numbering, the fixed sparsity pattern of A_{n-1} in
+// sliced-ELL form, static mass/stiffness values, edge-element incidences for the
+// per-step weighted stiffness, membrane tables, and the state accessors.
+// (Section 3.3 discretisation; Section 4.1 matrices M_r, A_r, A_r^{k,n},
+// M_{r,Gamma}, M_{rq,Gamma}; Section 2.3 initial state.)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "problem.h"
+
+namespace knp {
+
+namespace {
+
+// Position of column c in row r of the sliced-ELL pattern (rows sorted by column), -1 if absent.
+int64_t sell_find(const SellPattern& S, const std::vector<int32_t>& row_len, int64_t r, int32_t c) {
+    int64_t s = r / SELL_C, lane = r % SELL_C;
+    int64_t base = S.h_slice_ptr[s] + lane;
+    int32_t lo = 0, hi = row_len[r] - 1;
+    while (lo <= hi) {
+        int32_t mid = (lo + hi) / 2;
+        int32_t v = S.h_col[base + (int64_t)mid * SELL_C];
+        if (v == c) return base + (int64_t)mid * SELL_C;
+        if (v < c)
+            lo = mid + 1;
+        else
+            hi = mid - 1;
+    }
+    return -1;
+}
+
+double facet_area(const double* x, int dim, const int32_t* v) {
+    if (dim == 2) {
+        double dx = x[2 * (int64_t)v[1]] - x[2 * (int64_t)v[0]];
+        double dy = x[2 * (int64_t)v[1] + 1] - x[2 * (int64_t)v[0] + 1];
+        return std::sqrt(dx * dx + dy * dy);
+    }
+    double a[3], b[3];
+    for (int d = 0; d < 3; ++d) {
+        a[d] = x[3 * (int64_t)v[1] + d] - x[3 * (int64_t)v[0] + d];
+        b[d] = x[3 * (int64_t)v[2] + d] - x[3 * (int64_t)v[0] + d];
+    }
+    double c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+    return 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+}
+
+// |T| and barycentric gradients of a simplex (G[j][d] = d lambda_j / dx_d).
+void simplex_geometry(const double* x, int dim, const int32_t* el, double& vol, double G[4][3]) {
+    double J[3][3] = {{0}};
+    for (int j = 0; j < dim; ++j)
+        for (int d = 0; d < dim; ++d) J[d][j] = x[(int64_t)el[j + 1] * dim + d] - x[(int64_t)el[0] * dim + d];
+    double inv[3][3];
+    double det;
+    if (dim == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        inv[0][0] = J[1][1] / det;
+        inv[0][1] = -J[0][1] / det;
+        inv[1][0] = -J[1][0] / det;
+        inv[1][1] = J[0][0] / det;
+        vol = std::fabs(det) / 2.0;
+    } else {
+        det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+        inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+        inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+        inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        vol = std::fabs(det) / 6.0;
+    }
+    // lambda_{1..dim} = rows of J^{-1} applied to (x - x0)
+    for (int d = 0; d < dim; ++d) {
+        G[0][d] = 0.0;
+        for (int j = 0; j < dim; ++j) {
+            G[j + 1][d] = inv[j][d];
+            G[0][d] -= inv[j][d];
+        }
+    }
+}
+
+__global__ void k_init_state(double* u, int64_t N_i, int64_t n, double ci0, double ci1, double ci2, double ce0,
+                             double ce1, double ce2, double phiM0) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    bool in_i = g < N_i;
+    u[4 * g + 0] = in_i ? ci0 : ce0;
+    u[4 * g + 1] = in_i ? ci1 : ce1;
+    u[4 * g + 2] = in_i ? ci2 : ce2;
+    u[4 * g + 3] = in_i ? phiM0 : 0.0;
+}
+
+__global__ void k_init_gates(double* w, int64_t n_mv, double w0, double w1, double w2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_mv) return;
+    w[i] = w0;
+    w[n_mv + i] = w1;
+    w[2 * n_mv + i] = w2;
+}
+
+// Between the interleaved node-major layout and the API's region, ion-major arrays.
+__global__ void k_state_out(const double* u, int64_t N_i, int64_t N_e, double* c_i, double* phi_i, double* c_e,
+                            double* phi_e) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= N_i + N_e) return;
+    if (g < N_i) {
+        if (c_i)
+            for (int k = 0; k < KI; ++k) c_i[k * N_i + g] = u[4 * g + k];
+        if (phi_i) phi_i[g] = u[4 * g + 3];
+    } else {
+        int64_t j = g - N_i;
+        if (c_e)
+            for (int k = 0; k < KI; ++k) c_e[k * N_e + j] = u[4 * g + k];
+        if (phi_e) phi_e[j] = u[4 * g + 3];
+    }
+}
+
+__global__ void k_state_in(double* u, int64_t N_i, int64_t N_e, const double* c_i, const double* phi_i,
+                           const double* c_e, const double* phi_e) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= N_i + N_e) return;
+    if (g < N_i) {
+        if (c_i)
+            for (int k = 0; k < KI; ++k) u[4 * g + k] = c_i[k * N_i + g];
+        if (phi_i) u[4 * g + 3] = phi_i[g];
+    } else {
+        int64_t j = g - N_i;
+        if (c_e)
+            for (int k = 0; k < KI; ++k) u[4 * g + k] = c_e[k * N_e + j];
+        if (phi_e) u[4 * g + 3] = phi_e[j];
+    }
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void build_problem(knp_problem* P) {
+    const knp_mesh& m = *P->mesh;
+    const int dim = m.dim, nvpe = dim + 1;
+    const int64_t Ni = (int64_t)m.nodes_i.size(), Ne = (int64_t)m.nodes_e.size();
+    const int64_t n = Ni + Ne;
+    P->dim = dim;
+    P->N_i = Ni;
+    P->N_e = Ne;
+    P->n_nodes = n;
+    P->n_mv = (int64_t)m.mverts.size();
+    P->nf = m.nf();
+    P->n_elem = m.ne;
+    P->pin = (int32_t)(Ni + m.loc_e[m.pin_vertex]);
+    cudaStream_t st = P->stream;
+
+    // ---- elements with global node ids (intracellular first, then extracellular)
+    std::vector<int32_t> eln((size_t)m.ne * nvpe);
+    std::vector<int32_t> elem_src(m.ne);
+    {
+        int64_t k = 0;
+        for (int32_t e : m.elems_i) {
+            for (int j = 0; j < nvpe; ++j) eln[k * nvpe + j] = m.loc_i[m.elems[(int64_t)e * nvpe + j]];
+            elem_src[k++] = e;
+        }
+        for (int32_t e : m.elems_e) {
+            for (int j = 0; j < nvpe; ++j) eln[k * nvpe + j] = (int32_t)(Ni + m.loc_e[m.elems[(int64_t)e * nvpe + j]]);
+            elem_src[k++] = e;
+        }
+    }
+    // ---- node -> element incidence, then sorted neighbour lists per row
+    std::vector<int64_t> ne_ptr(n + 1, 0);
+    for (int64_t e = 0; e < m.ne; ++e)
+        for (int j = 0; j < nvpe; ++j) ne_ptr[eln[e * nvpe + j] + 1]++;
+    for (int64_t i = 0; i < n; ++i) ne_ptr[i + 1] += ne_ptr[i];
+    std::vector<int32_t> ne_list(ne_ptr[n]);
+    {
+        std::vector<int64_t> fill(ne_ptr.begin(), ne_ptr.end() - 1);
+        for (int64_t e = 0; e < m.ne; ++e)
+            for (int j = 0; j < nvpe; ++j) ne_list[fill[eln[e * nvpe + j]]++] = (int32_t)e;
+    }
+    std::vector<int32_t> row_len(n);
+    std::vector<std::vector<int32_t>> rows(n);
+    for (int64_t r = 0; r < n; ++r) {
+        auto& v = rows[r];
+        for (int64_t t = ne_ptr[r]; t < ne_ptr[r + 1]; ++t)
+            for (int j = 0; j < nvpe; ++j) v.push_back(eln[(int64_t)ne_list[t] * nvpe + j]);
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        row_len[r] = (int32_t)v.size();
+    }
+    // ---- sliced ELL
+    SellPattern& S = P->sell;
+    S.n_rows = n;
+    S.n_slices = (n + SELL_C - 1) / SELL_C;
+    S.h_slice_ptr.assign(S.n_slices + 1, 0);
+    for (int64_t s = 0; s < S.n_slices; ++s) {
+        int32_t w = 0;
+        for (int64_t r = s * SELL_C; r < std::min<int64_t>(n, (s + 1) * SELL_C); ++r) w = std::max(w, row_len[r]);
+        S.h_slice_ptr[s + 1] = S.h_slice_ptr[s] + (int64_t)w * SELL_C;
+    }
+    S.n_entries = S.h_slice_ptr[S.n_slices];
+    S.h_col.assign(S.n_entries, 0);
+    std::vector<int32_t> h_edge(S.n_entries, -2);
+    for (int64_t s = 0; s < S.n_slices; ++s) {
+        int64_t w = (S.h_slice_ptr[s + 1] - S.h_slice_ptr[s]) / SELL_C;
+        for (int64_t lane = 0; lane < SELL_C; ++lane) {
+            int64_t r = s * SELL_C + lane;
+            for (int64_t k = 0; k < w; ++k) {
+                int64_t pos = S.h_slice_ptr[s] + k * SELL_C + lane;
+                if (r < n && k < row_len[r]) {
+                    S.h_col[pos] = rows[r][k];
+                } else {
+                    S.h_col[pos] = (int32_t)std::min<int64_t>(r, n - 1);  // padding: own row, zero values
+                }
+            }
+        }
+    }
+    // ---- undirected edges j < l and their ids on both directed entries
+    int64_t n_edges = 0;
+    for (int64_t r = 0; r < n; ++r)
+        for (int32_t k = 0; k < row_len[r]; ++k) {
+            int32_t c = rows[r][k];
+            int64_t pos = S.h_slice_ptr[r / SELL_C] + (int64_t)k * SELL_C + r % SELL_C;
+            if (c == r)
+                h_edge[pos] = -1;
+            else if (c > r)
+                h_edge[pos] = (int32_t)n_edges++;
+        }
+    for (int64_t r = 0; r < n; ++r)
+        for (int32_t k = 0; k < row_len[r]; ++k) {
+            int32_t c = rows[r][k];
+            if (c < r) {
+                int64_t pos = S.h_slice_ptr[r / SELL_C] + (int64_t)k * SELL_C + r % SELL_C;
+                h_edge[pos] = h_edge[sell_find(S, row_len, c, (int32_t)r)];
+            }
+        }
+    P->n_edges = n_edges;
+    rows.clear();
+    rows.shrink_to_fit();
+    // ---- static M and A, and the edge incidence (element, a^T_jl)
+    std::vector<double> hm(S.n_entries, 0.0), ha(S.n_entries, 0.0);
+    std::vector<int32_t> e_cnt(n_edges + 1, 0);
+    std::vector<double> vol(m.ne);
+    std::vector<double> Ael((size_t)m.ne * 16);
+    for (int64_t e = 0; e < m.ne; ++e) {
+        double G[4][3];
+        simplex_geometry(m.coords.data(), dim, &m.elems[(int64_t)elem_src[e] * nvpe], vol[e], G);
+        for (int j = 0; j < nvpe; ++j)
+            for (int l = 0; l < nvpe; ++l) {
+                double s = 0;
+                for (int d = 0; d < dim; ++d) s += G[j][d] * G[l][d];
+                Ael[e * 16 + j * 4 + l] = vol[e] * s;
+            }
+    }
+    const double mdiag = (dim == 2) ? 1.0 / 6.0 : 1.0 / 10.0;   // (1+1)/((d+1)(d+2))
+    const double moff = (dim == 2) ? 1.0 / 12.0 : 1.0 / 20.0;
+    for (int64_t e = 0; e < m.ne; ++e) {
+        for (int j = 0; j < nvpe; ++j)
+            for (int l = 0; l < nvpe; ++l) {
+                int32_t r = eln[e * nvpe + j], c = eln[e * nvpe + l];
+                int64_t pos = sell_find(S, row_len, r, c);
+                hm[pos] += vol[e] * (j == l ? mdiag : moff);
+                ha[pos] += Ael[e * 16 + j * 4 + l];
+                if (j < l) {
+                    int32_t id = h_edge[pos];
+                    e_cnt[id + 1]++;
+                }
+            }
+    }
+    for (int64_t i = 0; i < n_edges; ++i) e_cnt[i + 1] += e_cnt[i];
+    std::vector<int32_t> h_einc(e_cnt[n_edges]);
+    std::vector<double> h_ecoef(e_cnt[n_edges]);
+    {
+        std::vector<int32_t> fill(e_cnt.begin(), e_cnt.end() - 1);
+        for (int64_t e = 0; e < m.ne; ++e)
+            for (int j = 0; j < nvpe; ++j)
+                for (int l = j + 1; l < nvpe; ++l) {
+                    int32_t r = eln[e * nvpe + j], c = eln[e * nvpe + l];
+                    int32_t id = h_edge[sell_find(S, row_len, r, c)];
+                    h_einc[fill[id]] = (int32_t)e;
+                    h_ecoef[fill[id]] = Ael[e * 16 + j * 4 + l];
+                    fill[id]++;
+                }
+    }
+    // ---- membrane
+    const int64_t nmv = P->n_mv, nf = P->nf;
+    std::vector<int32_t> h_mvg(2 * nmv);
+    for (int64_t a = 0; a < nmv; ++a) {
+        int32_t v = m.mverts[a];
+        h_mvg[a] = m.loc_i[v];
+        h_mvg[nmv + a] = (int32_t)(Ni + m.loc_e[v]);
+    }
+    std::vector<int32_t> h_fmv(nf * dim);
+    std::vector<double> h_farea(nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        for (int d = 0; d < dim; ++d) {
+            int32_t v = m.facets[f * dim + d];
+            h_fmv[f * dim + d] = (int32_t)(std::lower_bound(m.mverts.begin(), m.mverts.end(), v) - m.mverts.begin());
+        }
+        h_farea[f] = facet_area(m.coords.data(), dim, &m.facets[f * dim]);
+    }
+    std::vector<int32_t> h_mvf_ptr(nmv + 1, 0);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int d = 0; d < dim; ++d) h_mvf_ptr[h_fmv[f * dim + d] + 1]++;
+    for (int64_t a = 0; a < nmv; ++a) h_mvf_ptr[a + 1] += h_mvf_ptr[a];
+    std::vector<int32_t> h_mvf(h_mvf_ptr[nmv]);
+    {
+        std::vector<int32_t> fill(h_mvf_ptr.begin(), h_mvf_ptr.end() - 1);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int d = 0; d < dim; ++d) h_mvf[fill[h_fmv[f * dim + d]]++] = (int32_t)((f << 2) | d);
+    }
+    // membrane vertex pairs (a, b) sharing a facet, with the shared facets
+    struct PairInc {
+        int64_t key;
+        int32_t packed;
+    };
+    std::vector<PairInc> pinc;
+    pinc.reserve(nf * dim * dim);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int sa = 0; sa < dim; ++sa)
+            for (int sb = 0; sb < dim; ++sb) {
+                int64_t a = h_fmv[f * dim + sa], b = h_fmv[f * dim + sb];
+                pinc.push_back({a * nmv + b, (int32_t)((f << 4) | (sa << 2) | sb)});
+            }
+    std::sort(pinc.begin(), pinc.end(), [](const PairInc& x, const PairInc& y) {
+        return x.key < y.key || (x.key == y.key && x.packed < y.packed);
+    });
+    std::vector<int64_t> pair_key;
+    std::vector<int32_t> h_mp_ptr(1, 0), h_mpf;
+    for (size_t i = 0; i < pinc.size(); ++i) {
+        if (i == 0 || pinc[i].key != pinc[i - 1].key) {
+            pair_key.push_back(pinc[i].key);
+            h_mp_ptr.push_back(h_mp_ptr.back());
+        }
+        h_mpf.push_back(pinc[i].packed);
+        h_mp_ptr.back()++;
+    }
+    const int64_t npairs = (int64_t)pair_key.size();
+    P->n_pairs = npairs;
+    // cross-region CSR: row gi(a) -> col ge(b) and row ge(a) -> col gi(b)
+    std::vector<int32_t>& xp = P->h_xptr;
+    std::vector<int32_t>& xc = P->h_xcol;
+    xp.assign(n + 1, 0);
+    for (int64_t t = 0; t < npairs; ++t) {
+        int64_t a = pair_key[t] / nmv;
+        xp[h_mvg[a] + 1]++;
+        xp[h_mvg[nmv + a] + 1]++;
+    }
+    for (int64_t r = 0; r < n; ++r) xp[r + 1] += xp[r];
+    xc.assign(xp[n], 0);
+    std::vector<int32_t> h_tgt(4 * npairs);
+    {
+        std::vector<int32_t> fill(xp.begin(), xp.end() - 1);
+        // pairs are sorted by (a, b), so columns within a row come out sorted by b
+        for (int64_t t = 0; t < npairs; ++t) {
+            int64_t a = pair_key[t] / nmv, b = pair_key[t] % nmv;
+            int32_t gia = h_mvg[a], gea = h_mvg[nmv + a], gib = h_mvg[b], geb = h_mvg[nmv + b];
+            h_tgt[4 * t + 0] = (int32_t)sell_find(S, row_len, gia, gib);
+            h_tgt[4 * t + 1] = (int32_t)sell_find(S, row_len, gea, geb);
+            KNP_REQUIRE(h_tgt[4 * t] >= 0 && h_tgt[4 * t + 1] >= 0, KNP_ERR_INVALID_MESH,
+                        "membrane facet edge missing from the region pattern");
+            xc[fill[gia]] = geb;
+            h_tgt[4 * t + 2] = fill[gia]++;
+            xc[fill[gea]] = gib;
+            h_tgt[4 * t + 3] = fill[gea]++;
+        }
+    }
+    KNP_REQUIRE(S.n_entries < INT32_MAX, KNP_ERR_INVALID_ARG, "pattern too large for 32-bit positions");
+
+    // ---- uploads
+    S.slice_ptr.upload(S.h_slice_ptr, st);
+    S.col.upload(S.h_col, st);
+    P->sell_edge.upload(h_edge, st);
+    P->sell_m.upload(hm, st);
+    P->sell_a.upload(ha, st);
+    P->sell_e.alloc(3 * S.n_entries);
+    P->sell_e.zero(st);
+    P->xptr.upload(xp, st);
+    P->xcol.upload(xc, st);
+    P->xe.alloc(std::max<int64_t>(1, 3 * (int64_t)xc.size()));
+    P->xe.zero(st);
+    P->el_nodes.upload(eln, st);
+    P->cbar.alloc(3 * m.ne);
+    P->eptr.upload(e_cnt, st);
+    P->einc.upload(h_einc, st);
+    P->ecoef.upload(h_ecoef, st);
+    P->ak.alloc(std::max<int64_t>(1, 3 * n_edges));
+    P->mv_g.upload(h_mvg, st);
+    P->gates.alloc(3 * nmv);
+    P->gates_new.alloc(3 * nmv);
+    P->mfield.alloc(12 * nmv);
+    P->f_mv.upload(h_fmv, st);
+    P->f_area.upload(h_farea, st);
+    P->f_model.upload(P->facet_model, st);
+    P->f_gleak.upload(P->facet_gleak, st);
+    P->f_mask.upload(P->stim_mask, st);
+    P->mvf_ptr.upload(h_mvf_ptr, st);
+    P->mvf.upload(h_mvf, st);
+    P->mp_ptr.upload(h_mp_ptr, st);
+    P->mpf.upload(h_mpf, st);
+    P->mp_tgt.upload(h_tgt, st);
+    P->u.alloc(4 * n);
+    P->f.alloc(4 * n);
+    P->f.zero(st);
+    P->sinv.alloc(4 * n);
+    P->svec.alloc(4 * n);
+    const knp_problem_desc& d = P->desc;
+    k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
+                                          d.c_e0[2], d.phi_M0);
+    if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
+    KNP_CUDA(cudaGetLastError());
+    KNP_CUDA(cudaStreamSynchronize(st));
+}
+
+void download_state(const knp_problem* p, std::vector<double>& u) {
+    p->u.download(u, p->stream);
+    KNP_CUDA(cudaStreamSynchronize(p->stream));
+}
+
+void state_copy_out(const knp_problem* p, bool device, double* c_i, double* phi_i, double* c_e, double* phi_e) {
+    const int64_t Ni = p->N_i, Ne = p->N_e, n = Ni + Ne;
+    if (device) {
+        k_state_out<<<nblk(n), 256, 0, p->stream>>>(p->u.p, Ni, Ne, c_i, phi_i, c_e, phi_e);
+        KNP_CUDA(cudaGetLastError());
+        KNP_CUDA(cudaStreamSynchronize(p->stream));
+        return;
+    }
+    std::vector<double> u;
+    download_state(p, u);
+    for (int64_t g = 0; g < n; ++g) {
+        if (g < Ni) {
+            if (c_i)
+                for (int k = 0; k < KI; ++k) c_i[k * Ni + g] = u[4 * g + k];
+            if (phi_i) phi_i[g] = u[4 * g + 3];
+        } else {
+            int64_t j = g - Ni;
+            if (c_e)
+                for (int k = 0; k < KI; ++k) c_e[k * Ne + j] = u[4 * g + k];
+            if (phi_e) phi_e[j] = u[4 * g + 3];
+        }
+    }
+}
+
+void state_copy_in(knp_problem* p, bool device, const double* c_i, const double* phi_i, const double* c_e,
+                   const double* phi_e) {
+    const int64_t Ni = p->N_i, Ne = p->N_e, n = Ni + Ne;
+    if (device) {
+        k_state_in<<<nblk(n), 256, 0, p->stream>>>(p->u.p, Ni, Ne, c_i, phi_i, c_e, phi_e);
+        KNP_CUDA(cudaGetLastError());
+        return;
+    }
+    std::vector<double> u;
+    download_state(p, u);
+    for (int64_t g = 0; g < n; ++g) {
+        if (g < Ni) {
+            if (c_i)
+                for (int k = 0; k < KI; ++k) u[4 * g + k] = c_i[k * Ni + g];
+            if (phi_i) u[4 * g + 3] = phi_i[g];
+        } else {
+            int64_t j = g - Ni;
+            if (c_e)
+                for (int k = 0; k < KI; ++k) u[4 * g + k] = c_e[k * Ne + j];
+            if (phi_e) u[4 * g + 3] = phi_e[j];
+        }
+    }
+    KNP_CUDA(cudaMemcpyAsync(p->u.p, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    KNP_CUDA(cudaStreamSynchronize(p->stream));
+}
+
+}  // namespace knp

@@ -1,0 +1,153 @@
+// Device-side problem state and the kernels' parameter blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <vector>
+
+#include "common.h"
+
+namespace knp {
+
+#define KNP_CUDA(call)                                                                            \
+    do {                                                                                          \
+        cudaError_t _e = (call);                                                                  \
+        if (_e != cudaSuccess)                                                                    \
+            KNP_FAIL(_e == cudaErrorMemoryAllocation ? KNP_ERR_OOM : KNP_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                     cudaGetErrorString(_e), __FILE__, __LINE__);                                 \
+    } while (0)
+
+// Owning device array.
+template <class T>
+struct DArray {
+    T* p = nullptr;
+    size_t n = 0;
+    DArray() = default;
+    DArray(const DArray&) = delete;
+    DArray& operator=(const DArray&) = delete;
+    ~DArray() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) return;
+        KNP_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+        n = count;
+    }
+    void upload(const std::vector<T>& h, cudaStream_t s) {
+        alloc(h.size());
+        if (n) KNP_CUDA(cudaMemcpyAsync(p, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void download(std::vector<T>& h, cudaStream_t s) const {
+        h.resize(n);
+        if (n) KNP_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    }
+    void zero(cudaStream_t s) {
+        if (n) KNP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+};
+
+constexpr int KI = 3;          // ions handled by the kernels
+constexpr int NF = KI + 1;     // fields per node
+constexpr int SELL_C = 32;     // rows per slice of the sliced-ELL layout
+
+// Sliced ELLPACK pattern (slice height 32, column-major inside a slice).
+// Entry k of row r sits at slice_ptr[r/32] + k*32 + r%32. Padding entries
+// point at their own row and carry zero values.
+struct SellPattern {
+    int64_t n_rows = 0, n_slices = 0, n_entries = 0;
+    std::vector<int64_t> h_slice_ptr;
+    std::vector<int32_t> h_col;
+    DArray<int64_t> slice_ptr;
+    DArray<int32_t> col;
+};
+
+// Physical constants of one region as the kernels see them.
+struct RegionCoef {
+    double tau[KI];    // tau_r^k = dt D_r^k
+    double taut[KI];   // tau~_r^k = tau_r^k z_k / psi
+};
+
+struct StepParams {
+    double z[KI];
+    double R, T, F, Cm, dt, psi;
+    RegionCoef reg[2];     // 0 = i, 1 = e
+    int32_t ion_na, ion_k;
+    double gbar_na, gbar_k, phi_rest;
+    int32_t n_ode;
+    double g_stim;         // stimulus conductance at t_{n-1}
+};
+
+struct AmgHierarchy;        // vcycle.cu
+struct GmresWork;           // gmres.cu
+
+}  // namespace knp
+
+struct knp_problem {
+    const knp_mesh* mesh = nullptr;
+    cudaStream_t stream = nullptr;
+    knp::StepParams sp{};
+    knp_problem_desc desc{};
+    std::vector<int32_t> facet_model;
+    std::vector<double> facet_gleak;
+    std::vector<uint8_t> stim_mask;
+    int32_t dim = 0;
+    int64_t N_i = 0, N_e = 0, n_nodes = 0, n_mv = 0, nf = 0, n_elem = 0, n_edges = 0, n_pairs = 0;
+    int32_t pin = -1;               // global node of the pinned phi_e
+    double t = 0.0;
+    int64_t step_index = 0;
+    bool assembled = false;
+
+    // operator A (region-internal part in SELL; cross-region membrane part in CSR)
+    knp::SellPattern sell;
+    knp::DArray<int32_t> sell_edge;      // undirected edge id, -1 diagonal, -2 padding
+    knp::DArray<double> sell_m, sell_a;  // static mass and stiffness
+    knp::DArray<double> sell_e;          // [3][n_entries] c^k-row phi-col coefficients (per step)
+    std::vector<int32_t> h_xptr, h_xcol;
+    knp::DArray<int32_t> xptr, xcol;     // cross-region entries, CSR over rows
+    knp::DArray<double> xe;              // [3][n_cross]
+
+    // bulk assembly data
+    knp::DArray<int32_t> el_nodes;       // [n_elem][dim+1] global node ids
+    knp::DArray<double> cbar;            // [3][n_elem] element means of c^k
+    knp::DArray<int32_t> eptr, einc;     // edge -> incident elements (CSR)
+    knp::DArray<double> ecoef;           // element stiffness entry a^T_jl per incidence
+    knp::DArray<double> ak;              // [3][n_edges] weighted stiffness per edge
+
+    // membrane data
+    knp::DArray<int32_t> mv_g;           // [2][n_mv] global i-node and e-node of each membrane vertex
+    knp::DArray<double> gates;           // [3][n_mv] (n, m, h) of the committed state w_{n-1}
+    knp::DArray<double> gates_new;       // [3][n_mv] w_n computed by the last assembly
+    knp::DArray<double> mfield;          // [12][n_mv]: phiM, C_i(3), C_e(3), q_leak(3), q_hhna, q_hhk
+    knp::DArray<int32_t> f_mv;           // [nf][dim] membrane-vertex index of facet vertices
+    knp::DArray<double> f_area;
+    knp::DArray<int32_t> f_model;
+    knp::DArray<double> f_gleak;         // [nf][3]
+    knp::DArray<uint8_t> f_mask;
+    knp::DArray<int32_t> mvf_ptr, mvf;   // membrane vertex -> incident facets, packed (facet << 2 | local)
+    knp::DArray<int32_t> mp_ptr, mpf;    // membrane vertex pair -> shared facets, packed (f << 4 | sa << 2 | sb)
+    knp::DArray<int32_t> mp_tgt;         // [n_pairs][4]: SELL pos (i), SELL pos (e), cross pos (i row), cross pos (e row)
+
+    // vectors [n_nodes][4]
+    knp::DArray<double> u;               // state u_{n-1} / u_n
+    knp::DArray<double> f;               // right-hand side f_n
+    knp::DArray<double> sinv;            // 1/sqrt(diag P_0) (set by knp_amg_setup)
+    knp::DArray<double> svec;            // sqrt(diag P_0)
+
+    knp::AmgHierarchy* amg = nullptr;
+    knp::GmresWork* gw = nullptr;
+    ~knp_problem();
+};
+
+namespace knp {
+// assemble.cu
+void launch_assembly(knp_problem* p);
+// spmv.cu
+// y = A x (unscaled), or with row scaling / residual; see spmv.cu
+void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b);
+void download_state(const knp_problem* p, std::vector<double>& u);
+}  // namespace knp

@@ -1,0 +1,108 @@
+// y = A_{n-1} x on the node-block structure of Section 4.1.
+//
+// Per directed same-region entry (j, l) the operator stores five numbers: the mass
+// m_jl and stiffness a_jl (static) and e^k_jl = tau~_r^k A_r^{k,n-1}_jl + [C_r^k M_{r,Gamma}]_jl
+// (per step). The 4x4 node block of A_r^n is then
+//     c^k row:  (m + tau_r^k a) on c^k,   e^k on phi_r
+//     phi row:  z_k tau_r^k a on c^k,     sum_k z_k e^k on phi_r
+// because sum_k z_k C_r^k = C_m/F (sum_k alpha_r^k = 1). Cross-region membrane entries
+// (B_rq) carry -[C_r^k M_{rq,Gamma}] in the same e^k slot with m = a = 0. Per entry the
+// kernel needs nine FMAs (sum m x^k, sum a x^k, sum e^k phi) instead of sixteen.
+// One thread per row; the sliced-ELL layout makes the value loads of a warp contiguous.
+#include "problem.h"
+
+namespace knp {
+
+namespace {
+
+struct OpArgs {
+    int64_t n, N_i, n_entries;
+    int32_t pin;
+    const int64_t* slice_ptr;
+    const int32_t* col;
+    const double* m;
+    const double* a;
+    const double* e;
+    const int32_t* xptr;
+    const int32_t* xcol;
+    const double* xe;
+    int64_t n_cross;
+    double tau[2][KI];
+    double z[KI];
+};
+
+// y = rowscale .* (b - A x)  (b, rowscale optional)
+__global__ void __launch_bounds__(128) k_op_apply(OpArgs A, const double* __restrict__ x, double* __restrict__ y,
+                                                  const double* __restrict__ rowscale, const double* __restrict__ b) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= A.n) return;
+    const int reg = r < A.N_i ? 0 : 1;
+    int64_t s = r / SELL_C;
+    int64_t base = A.slice_ptr[s] + r % SELL_C;
+    int64_t w = (A.slice_ptr[s + 1] - A.slice_ptr[s]) / SELL_C;
+    double am[KI] = {0, 0, 0}, aa[KI] = {0, 0, 0}, ae[KI] = {0, 0, 0};
+    for (int64_t k = 0; k < w; ++k) {
+        int64_t pos = base + k * SELL_C;
+        int64_t c = A.col[pos];
+        const double2* xp = reinterpret_cast<const double2*>(x + 4 * c);
+        double2 x01 = xp[0], x23 = xp[1];
+        double mv = A.m[pos], av = A.a[pos];
+        am[0] += mv * x01.x;
+        am[1] += mv * x01.y;
+        am[2] += mv * x23.x;
+        aa[0] += av * x01.x;
+        aa[1] += av * x01.y;
+        aa[2] += av * x23.x;
+        ae[0] += A.e[pos] * x23.y;
+        ae[1] += A.e[A.n_entries + pos] * x23.y;
+        ae[2] += A.e[2 * A.n_entries + pos] * x23.y;
+    }
+    for (int t = A.xptr[r]; t < A.xptr[r + 1]; ++t) {
+        double phi = x[4 * (int64_t)A.xcol[t] + 3];
+        for (int k = 0; k < KI; ++k) ae[k] += A.xe[k * A.n_cross + t] * phi;
+    }
+    double out[4];
+    out[3] = 0.0;
+    for (int k = 0; k < KI; ++k) {
+        double ta = A.tau[reg][k] * aa[k];
+        out[k] = am[k] + ta + ae[k];
+        out[3] += A.z[k] * (ta + ae[k]);
+    }
+    if (r == A.pin) out[3] = x[4 * r + 3];
+    if (b) {
+        for (int k = 0; k < 4; ++k) out[k] = b[4 * r + k] - out[k];
+    }
+    if (rowscale) {
+        for (int k = 0; k < 4; ++k) out[k] *= rowscale[4 * r + k];
+    }
+    double2* yp = reinterpret_cast<double2*>(y + 4 * r);
+    yp[0] = make_double2(out[0], out[1]);
+    yp[1] = make_double2(out[2], out[3]);
+}
+
+}  // namespace
+
+void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b) {
+    OpArgs A;
+    A.n = p->n_nodes;
+    A.N_i = p->N_i;
+    A.n_entries = p->sell.n_entries;
+    A.pin = p->pin;
+    A.slice_ptr = p->sell.slice_ptr.p;
+    A.col = p->sell.col.p;
+    A.m = p->sell_m.p;
+    A.a = p->sell_a.p;
+    A.e = p->sell_e.p;
+    A.xptr = p->xptr.p;
+    A.xcol = p->xcol.p;
+    A.xe = p->xe.p;
+    A.n_cross = (int64_t)p->h_xcol.size();
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < KI; ++k) A.tau[r][k] = p->sp.reg[r].tau[k];
+    for (int k = 0; k < KI; ++k) A.z[k] = p->sp.z[k];
+    unsigned blocks = (unsigned)((A.n + 127) / 128);
+    k_op_apply<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
+    KNP_CUDA(cudaGetLastError());
+}
+
+}  // namespace knp

@@ -1,0 +1,233 @@
+// Mesh intake: membrane facets, duplicated membrane nodes, region numbering, pin
+// (Section 3.3 spatial discretisation; Remark 4.1 point pin).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <numeric>
+
+#include "common.h"
+
+namespace knp {
+
+thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+struct FacetKey {
+    int32_t v[3];
+    int32_t elem;
+    int32_t opp;
+};
+
+double simplex_det(const double* x, int dim, const int32_t* el) {
+    if (dim == 2) {
+        const double* a = x + 2 * (int64_t)el[0];
+        const double* b = x + 2 * (int64_t)el[1];
+        const double* c = x + 2 * (int64_t)el[2];
+        return (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]);
+    }
+    const double* a = x + 3 * (int64_t)el[0];
+    double e[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int d = 0; d < 3; ++d) e[j][d] = x[3 * (int64_t)el[j + 1] + d] - a[d];
+    return e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+}
+
+}  // namespace
+
+void build_topology(knp_mesh& m) {
+    const int dim = m.dim;
+    const int nvpe = dim + 1;
+    const int64_t ne = m.ne, nv = m.nv;
+    // element checks
+    double max_abs = 0.0;
+    for (int64_t i = 0; i < nv * dim; ++i) max_abs = std::max(max_abs, std::fabs(m.coords[i]));
+    for (int64_t e = 0; e < ne; ++e) {
+        const int32_t* el = &m.elems[e * nvpe];
+        for (int j = 0; j < nvpe; ++j)
+            KNP_REQUIRE(el[j] >= 0 && el[j] < nv, KNP_ERR_INVALID_ARG, "element %lld has vertex id %d out of range",
+                        (long long)e, el[j]);
+        KNP_REQUIRE(m.tag[e] >= 0, KNP_ERR_INVALID_ARG, "negative tag on element %lld", (long long)e);
+        double det = simplex_det(m.coords.data(), dim, el);
+        KNP_REQUIRE(std::fabs(det) > 1e-14 * std::pow(max_abs, dim) && std::isfinite(det), KNP_ERR_INVALID_MESH,
+                    "element %lld is degenerate", (long long)e);
+    }
+    // facets: slot s of element e is the facet opposite local vertex s
+    std::vector<FacetKey> keys((size_t)ne * nvpe);
+    for (int64_t e = 0; e < ne; ++e) {
+        const int32_t* el = &m.elems[e * nvpe];
+        for (int s = 0; s < nvpe; ++s) {
+            FacetKey k{{-1, -1, -1}, (int32_t)e, s};
+            int c = 0;
+            for (int j = 0; j < nvpe; ++j)
+                if (j != s) k.v[c++] = el[j];
+            std::sort(k.v, k.v + dim);
+            keys[e * nvpe + s] = k;
+        }
+    }
+    auto less = [dim](const FacetKey& a, const FacetKey& b) {
+        for (int d = 0; d < dim; ++d)
+            if (a.v[d] != b.v[d]) return a.v[d] < b.v[d];
+        return a.elem < b.elem;
+    };
+    auto same = [dim](const FacetKey& a, const FacetKey& b) {
+        for (int d = 0; d < dim; ++d)
+            if (a.v[d] != b.v[d]) return false;
+        return true;
+    };
+    std::sort(keys.begin(), keys.end(), less);
+    std::vector<FacetKey> mem;  // intracellular side of each membrane facet
+    for (size_t i = 0; i + 1 < keys.size(); ++i) {
+        if (!same(keys[i], keys[i + 1])) continue;
+        KNP_REQUIRE(i + 2 >= keys.size() || !same(keys[i], keys[i + 2]), KNP_ERR_INVALID_MESH,
+                    "a facet is shared by more than two elements");
+        int32_t ta = m.tag[keys[i].elem], tb = m.tag[keys[i + 1].elem];
+        if (ta != tb) {
+            KNP_REQUIRE(ta == 0 || tb == 0, KNP_ERR_INVALID_MESH, "cells %d and %d share a facet", ta, tb);
+            mem.push_back(ta > 0 ? keys[i] : keys[i + 1]);
+        }
+        ++i;
+    }
+    // keys are sorted lexicographically, so mem is in facet order already
+    const int64_t nf = (int64_t)mem.size();
+    m.facets.resize(nf * dim);
+    m.facet_elem_i.resize(nf);
+    m.facet_opp_i.resize(nf);
+    m.facet_cell.resize(nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        for (int d = 0; d < dim; ++d) m.facets[f * dim + d] = mem[f].v[d];
+        m.facet_elem_i[f] = mem[f].elem;
+        m.facet_opp_i[f] = mem[f].opp;
+        m.facet_cell[f] = m.tag[mem[f].elem];
+    }
+    std::vector<char> in_i(nv, 0), in_e(nv, 0), on_g(nv, 0);
+    std::vector<int32_t> vcell(nv, 0);
+    m.n_cells = 0;
+    for (int64_t e = 0; e < ne; ++e) {
+        const int32_t* el = &m.elems[e * nvpe];
+        int32_t t = m.tag[e];
+        m.n_cells = std::max(m.n_cells, t);
+        if (t > 0) {
+            m.elems_i.push_back((int32_t)e);
+            for (int j = 0; j < nvpe; ++j) {
+                int32_t v = el[j];
+                KNP_REQUIRE(vcell[v] == 0 || vcell[v] == t, KNP_ERR_INVALID_MESH,
+                            "vertex %d belongs to cells %d and %d", v, vcell[v], t);
+                vcell[v] = t;
+                in_i[v] = 1;
+            }
+        } else {
+            m.elems_e.push_back((int32_t)e);
+            for (int j = 0; j < nvpe; ++j) in_e[el[j]] = 1;
+        }
+    }
+    for (int64_t i = 0; i < nf * dim; ++i) on_g[m.facets[i]] = 1;
+    for (int64_t v = 0; v < nv; ++v)
+        KNP_REQUIRE((in_i[v] && in_e[v]) == (bool)on_g[v], KNP_ERR_INVALID_MESH,
+                    "vertex %lld touches both regions outside the membrane facets", (long long)v);
+    std::vector<char> cell_has_facet(m.n_cells + 1, 0);
+    for (int64_t f = 0; f < nf; ++f) cell_has_facet[m.facet_cell[f]] = 1;
+    std::vector<char> cell_present(m.n_cells + 1, 0);
+    for (int32_t e : m.elems_i) cell_present[m.tag[e]] = 1;
+    for (int c = 1; c <= m.n_cells; ++c)
+        KNP_REQUIRE(!cell_present[c] || cell_has_facet[c], KNP_ERR_INVALID_MESH, "cell %d has no membrane facet", c);
+    KNP_REQUIRE(!m.elems_e.empty(), KNP_ERR_INVALID_MESH, "no extracellular elements");
+    m.loc_i.assign(nv, -1);
+    m.loc_e.assign(nv, -1);
+    for (int64_t v = 0; v < nv; ++v) {
+        if (in_i[v]) {
+            m.loc_i[v] = (int32_t)m.nodes_i.size();
+            m.nodes_i.push_back((int32_t)v);
+            m.node_cell_i.push_back(vcell[v]);
+        }
+        if (in_e[v]) {
+            m.loc_e[v] = (int32_t)m.nodes_e.size();
+            m.nodes_e.push_back((int32_t)v);
+        }
+        if (on_g[v]) m.mverts.push_back((int32_t)v);
+    }
+    // pin: extracellular vertex nearest to the origin, ties by lowest id
+    double best = INFINITY;
+    for (int32_t v : m.nodes_e) {
+        double d2 = 0;
+        for (int d = 0; d < dim; ++d) d2 += m.coords[(int64_t)v * dim + d] * m.coords[(int64_t)v * dim + d];
+        if (d2 < best) {
+            best = d2;
+            m.pin_vertex = v;
+        }
+    }
+}
+
+}  // namespace knp
+
+using namespace knp;
+
+extern "C" {
+
+const char* knp_last_error(void) { return g_last_error.c_str(); }
+
+knp_status knp_mesh_create(const knp_mesh_desc* d, knp_mesh** out) {
+    return guarded([&] {
+        KNP_REQUIRE(d && out, KNP_ERR_INVALID_ARG, "NULL argument");
+        *out = nullptr;
+        KNP_REQUIRE(d->dim == 2 || d->dim == 3, KNP_ERR_INVALID_ARG, "dim must be 2 or 3 (got %d)", d->dim);
+        KNP_REQUIRE(d->n_vertices > 0 && d->n_elems > 0 && d->coords && d->elems && d->elem_tag, KNP_ERR_INVALID_ARG,
+                    "empty mesh or NULL array");
+        KNP_REQUIRE(d->n_vertices < INT32_MAX && d->n_elems * (d->dim + 1) < INT32_MAX, KNP_ERR_INVALID_ARG,
+                    "mesh too large for 32-bit ids");
+        auto m = new knp_mesh();
+        try {
+            m->dim = d->dim;
+            m->nv = d->n_vertices;
+            m->ne = d->n_elems;
+            m->coords.assign(d->coords, d->coords + d->n_vertices * d->dim);
+            m->elems.assign(d->elems, d->elems + d->n_elems * (d->dim + 1));
+            m->tag.assign(d->elem_tag, d->elem_tag + d->n_elems);
+            build_topology(*m);
+        } catch (...) {
+            delete m;
+            throw;
+        }
+        *out = m;
+    });
+}
+
+knp_status knp_mesh_get_info(const knp_mesh* m, knp_mesh_info* info) {
+    return guarded([&] {
+        KNP_REQUIRE(m && info, KNP_ERR_INVALID_ARG, "NULL argument");
+        info->dim = m->dim;
+        info->n_vertices = m->nv;
+        info->n_elems = m->ne;
+        info->N_i = (int64_t)m->nodes_i.size();
+        info->N_e = (int64_t)m->nodes_e.size();
+        info->n_facets = m->nf();
+        info->n_membrane_vertices = (int64_t)m->mverts.size();
+        info->n_cells = m->n_cells;
+        info->pin_vertex = m->pin_vertex;
+        info->n_dof = (info->N_i + info->N_e) * 4;
+    });
+}
+
+knp_status knp_mesh_nodes(const knp_mesh* m, int32_t* nodes_i, int32_t* nodes_e) {
+    return guarded([&] {
+        KNP_REQUIRE(m, KNP_ERR_INVALID_ARG, "NULL mesh");
+        if (nodes_i) std::copy(m->nodes_i.begin(), m->nodes_i.end(), nodes_i);
+        if (nodes_e) std::copy(m->nodes_e.begin(), m->nodes_e.end(), nodes_e);
+    });
+}
+
+knp_status knp_mesh_facets(const knp_mesh* m, int32_t* vertices, int32_t* elem_i, int32_t* opp_i, int32_t* cell) {
+    return guarded([&] {
+        KNP_REQUIRE(m, KNP_ERR_INVALID_ARG, "NULL mesh");
+        if (vertices) std::copy(m->facets.begin(), m->facets.end(), vertices);
+        if (elem_i) std::copy(m->facet_elem_i.begin(), m->facet_elem_i.end(), elem_i);
+        if (opp_i) std::copy(m->facet_opp_i.begin(), m->facet_opp_i.end(), opp_i);
+        if (cell) std::copy(m->facet_cell.begin(), m->facet_cell.end(), cell);
+    });
+}
+
+void knp_mesh_destroy(knp_mesh* m) { delete m; }
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Assembly (entries of A_{n-1}, f_n), the operator apply, and full time steps (membrane
+update + assembly + AMG-preconditioned FGMRES) are compared element by element on the
+same seeded synthetic inputs. Bar: relative l2 error <= 1e-8 on the concentrations and
+on the potentials at every step (FGMRES rtol 1e-10), for the FP64 and FP32 hierarchies.
+"""
+import numpy as np
+import pytest
+
+from helpers import (blockscaled_entry_error, blockwise_vector_error, oracle_run, rel_errors)
+from oracle import problem as oproblem, system as osystem
+from synth import make_config
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _cfgs():
+    return {
+        "cfg1-2d-leak": make_config(1),
+        "cfg2-3d-hh-16": make_config(2).with_nx(16),
+        "cfg4-2d-16cells-32": make_config(4).with_nx(32),
+    }
+
+
+@pytest.mark.parametrize("name", list(_cfgs()))
+def test_assembly_and_operator(name):
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = _cfgs()[name]
+    pb, s0 = oproblem.from_config(cfg)
+    A, f, _ = osystem.assemble(pb, s0)
+    _, prob = problem_from_config(cfg)
+    prob.assemble_step()
+    Acoo = A.tocoo()
+    vals = prob.operator_entries(Acoo.row, Acoo.col)
+    assert blockscaled_entry_error(pb, A, vals) < 1e-12
+    assert blockwise_vector_error(pb, prob.rhs_get(), f) < 1e-12
+    x = np.random.default_rng(3).standard_normal(A.shape[0])
+    assert blockwise_vector_error(pb, prob.apply_operator(x), A @ x) < 1e-12
+    # nothing outside the oracle's pattern: entries at random off-pattern positions are zero
+    rng = np.random.default_rng(4)
+    r = rng.integers(0, A.shape[0], 2000)
+    c = rng.integers(0, A.shape[0], 2000)
+    off = np.asarray(A[r, c]).ravel() == 0
+    assert np.all(prob.operator_entries(r[off], c[off]) == 0)
+
+
+STEP_CASES = [("cfg1-2d-leak", 10, "direct"), ("cfg2-3d-hh-16", 8, "lu_p0"), ("cfg4-2d-16cells-32", 5, "direct")]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64-amg", "fp32-amg"])
+@pytest.mark.parametrize("name,n_steps,exact", STEP_CASES)
+def test_time_steps_match_oracle(name, n_steps, exact, precision):
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = _cfgs()[name]
+    pb, ref = oracle_run(cfg, n_steps, exact)
+    _, prob = problem_from_config(cfg)
+    prob.amg_setup(precision=precision)
+    for n in range(1, n_steps + 1):
+        st = prob.step(1, rtol=1e-10)
+        s = prob.state_get()
+        ec, ep = rel_errors(s, ref[n])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep, st)
+        # w_1 comes from the exact u_0; later gates inherit the solver's error in phi_M
+        np.testing.assert_allclose(s["w"], ref[n].w, rtol=1e-12 if n == 1 else TOL, atol=1e-14)
+        assert abs(s["t"] - n * cfg.dt) < 1e-15
+
+
+@pytest.mark.slow
+def test_config3_subset_125_cells_mixed():
+    """The 125-cell workload at its 32^3 version (192,748 unknowns), FP32 hierarchy, 3 steps."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(3).with_nx(32)
+    pb, ref = oracle_run(cfg, 3, "lu_p0")
+    _, prob = problem_from_config(cfg)
+    prob.amg_setup(precision=1)
+    for n in range(1, 4):
+        prob.step(1, rtol=1e-10)
+        ec, ep = rel_errors(prob.state_get(), ref[n])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep)
+
+
+def test_pin_on_a_membrane_vertex():
+    """A cell in the corner: the pinned extracellular node is a membrane node."""
+    from paper_2403_04491_gb300 import Mesh, problem_from_config
+    from dataclasses import replace
+    cfg = make_config(1)
+    cfg = replace(cfg, _mesh=None)
+    # build the mesh by hand (the synthetic generator keeps cells off the boundary): the cell
+    # covers the origin corner, so the extracellular vertex nearest to the origin is on Gamma
+    from synth.mesh import structured_mesh, StructuredMesh
+    coords, elems = structured_mesh(2, 32, cfg.length)
+    cen = coords[elems].mean(axis=1) / cfg.length * 32
+    tag = ((cen[:, 0] < 8) & (cen[:, 1] < 16)).astype(np.int32)
+    cfg._mesh = StructuredMesh(2, 32, coords, elems, tag, np.zeros((1, 2, 2)), cfg.length)
+    mesh = Mesh(coords, elems, tag)
+    pb, ref = oracle_run(cfg, 3, "direct")
+    assert pb.topo.pin_vertex in set(pb.topo.membrane_vertices.tolist())
+    _, prob = problem_from_config(cfg, mesh=mesh)
+    pb0, s0 = oproblem.from_config(cfg)
+    A, f, _ = osystem.assemble(pb0, s0)
+    prob.assemble_step()
+    Acoo = A.tocoo()
+    assert blockscaled_entry_error(pb0, A, prob.operator_entries(Acoo.row, Acoo.col)) < 1e-12
+    prob.amg_setup()
+    for n in range(1, 4):
+        prob.step(1, rtol=1e-10)
+        ec, ep = rel_errors(prob.state_get(), ref[n])
+        assert ec <= TOL and ep <= TOL
+
+
+def test_state_roundtrip_and_resume():
+    """knp_state_get / knp_state_set: a run resumed from a saved state matches the straight run."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2).with_nx(12)
+    _, a = problem_from_config(cfg)
+    a.amg_setup()
+    a.step(2, rtol=1e-10)
+    saved = a.state_get()
+    a.step(2, rtol=1e-10)
+    end_a = a.state_get()
+    _, b = problem_from_config(cfg)
+    b.amg_setup()
+    b.state_set(saved["c_i"], saved["phi_i"], saved["c_e"], saved["phi_e"], saved["w"], saved["t"])
+    b.step(2, rtol=1e-10)
+    end_b = b.state_get()
+    for k in ("c_i", "phi_i", "c_e", "phi_e", "w"):
+        np.testing.assert_array_equal(end_a[k], end_b[k])
+    assert end_a["t"] == end_b["t"]

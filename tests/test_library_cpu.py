@@ -1,0 +1,99 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point that include/knp.h
+declares, and its host-side topology (knp_mesh_create) matches the oracle's. No GPU call."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.topology import build_topology
+from synth import make_config
+from synth.configs import model_a
+from synth.mesh import structured_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_04491_gb300.build import build_library
+    build_library()
+    from paper_2403_04491_gb300 import knp
+    return knp.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "knp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(knp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_2403_04491_gb300 import knp
+    assert set(declared_functions()) == set(knp.SIGNATURES)
+
+
+@pytest.mark.parametrize("cfg", [make_config(1), make_config(4), model_a(3, 8, 1e-4), make_config(3).with_nx(32)])
+def test_mesh_topology_matches_oracle(lib, cfg):
+    from paper_2403_04491_gb300 import Mesh
+    m = cfg.mesh
+    M = Mesh(m.coords, m.elems, m.elem_tag)
+    T = build_topology(m.coords, m.elems, m.elem_tag)
+    ni, ne = M.nodes()
+    v, e, o, c = M.facets()
+    assert M.info["n_dof"] == T.n_dof(3)
+    assert np.array_equal(ni, T.nodes_i) and np.array_equal(ne, T.nodes_e)
+    assert np.array_equal(v, T.facets) and np.array_equal(e, T.facet_elem_i)
+    assert np.array_equal(o, T.facet_opp_i) and np.array_equal(c, T.facet_cell)
+    assert M.info["pin_vertex"] == T.pin_vertex
+    assert M.info["n_cells"] == int(m.elem_tag.max())
+
+
+def test_config3_subset_count(lib):
+    # the 32^3 version of the 125-cell workload: 192,748 unknowns
+    from paper_2403_04491_gb300 import Mesh
+    m = make_config(3).with_nx(32).mesh
+    assert Mesh(m.coords, m.elems, m.elem_tag).info["n_dof"] == 192748
+
+
+def _two_cell_mesh(touch):
+    coords, elems = structured_mesh(2, 6, 1.0)
+    cen = coords[elems].mean(axis=1) * 6
+    tag = np.zeros(len(elems), np.int32)
+    tag[(cen[:, 0] > 1) & (cen[:, 0] < 3) & (cen[:, 1] > 1) & (cen[:, 1] < 3)] = 1
+    if touch == "facet":
+        tag[(cen[:, 0] > 3) & (cen[:, 0] < 5) & (cen[:, 1] > 1) & (cen[:, 1] < 3)] = 2
+    else:
+        tag[(cen[:, 0] > 3) & (cen[:, 0] < 5) & (cen[:, 1] > 3) & (cen[:, 1] < 5)] = 2
+    return coords, elems, tag
+
+
+@pytest.mark.parametrize("touch", ["facet", "vertex"])
+def test_invalid_meshes_are_rejected(lib, touch):
+    from paper_2403_04491_gb300 import KnpError, Mesh
+    coords, elems, tag = _two_cell_mesh(touch)
+    with pytest.raises(KnpError) as ei:
+        Mesh(coords, elems, tag)
+    assert ei.value.code == 2
+
+
+def test_invalid_arguments_are_rejected(lib):
+    from paper_2403_04491_gb300 import KnpError, Mesh
+    coords, elems = structured_mesh(2, 2, 1.0)
+    bad = elems.copy()
+    bad[0, 0] = 999
+    with pytest.raises(KnpError) as ei:
+        Mesh(coords, bad, np.zeros(len(elems), np.int32))
+    assert ei.value.code == 1
+    flat = coords.copy()
+    flat[:, 1] = 0.0   # every element degenerate
+    with pytest.raises(KnpError) as ei:
+        Mesh(flat, elems, np.zeros(len(elems), np.int32))
+    assert ei.value.code == 2
