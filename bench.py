@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the KNP-EMI time step (membrane update + assembly + AMG-preconditioned FGMRES).
+
+Workload: the 3D Hodgkin-Huxley scenario on the 64^3 Kuhn mesh of a 100 um cube with one
+box cell [0.3, 0.7]^3 (1,114,732 unknowns), stimulus 40 S/m^2 on facets with x < 40 um for
+t < 1 ms, dt = 0.05 ms, FGMRES(30) rtol 1e-10, FP64 hierarchy. One "step" is one IMEX time
+step; the metric is unknowns x time steps per second. AMG setup (once per run, on P_0) and
+topology are excluded, as the paper's "initialization" is; they are reported separately.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path does not shard on
+this single-GPU pool); value = unknowns x steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*timesteps/s (assembly+AMG-GMRES)"
+UNIT = "DOF*steps/s"
+WORKLOAD = "3D HH, 64^3 Kuhn tets, 100 um cube, cell [0.3,0.7]^3, 1,114,732 DOF, dt 0.05 ms, rtol 1e-10"
+PROFILE_FILE = os.path.join(ROOT, "profiles", "roofline_counters.json")
+SAMPLE_NX = 24   # oracle sample: the same scenario on the 24^3 version of its mesh
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- oracle legs
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from synth import make_config
+from oracle import problem, solve, step, system
+cfg = make_config(2).with_nx({nx})
+t0 = time.perf_counter()
+pb, s = problem.from_config(cfg)
+M = solve.lu_P0(system.preconditioner_P0(pb, s))
+t_setup = time.perf_counter() - t0
+for _ in range({warmup}):
+    s, _ = step.step(pb, s, method="gmres", M=M, rtol=1e-13)
+times = []
+for _ in range({steps}):
+    t = time.perf_counter()
+    s, _ = step.step(pb, s, method="gmres", M=M, rtol=1e-13)
+    times.append(time.perf_counter() - t)
+print(json.dumps(dict(n_dof=int(pb.topo.n_dof(3)), setup_s=t_setup, times=times)))
+"""
+
+
+def run_oracle(steps, warmup, nx=SAMPLE_NX):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, steps=steps, warmup=warmup)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_desc(nx, steps):
+    return (f"oracle (numpy/scipy FP64, 1 thread) on the same scenario at {nx}^3 (same cell, stimulus, dt); "
+            f"{steps} steps of assembly + GMRES(30) with LU(P_0) to 1e-13, after 1 untimed step")
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    r = run_oracle(args.steps, args.warmup)
+    tot = sum(r["times"])
+    value = r["n_dof"] * len(r["times"]) / tot
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * tot / len(r["times"]), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD + f" (oracle sample at {SAMPLE_NX}^3, {r['n_dof']} DOF)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                                  sample=oracle_sample_desc(SAMPLE_NX, args.steps)),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("vcycle.cu", "problem.h", "amg_setup.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2403_04491_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dominant_kernel_bytes(prob, precision):
+    """Algorithmic bytes of one finest-level Chebyshev step: the operator once (column index +
+    four values per stored entry) and six node vectors (x gathered, x itself, b, D^-1, d in/out
+    counted as the update reads d and writes d and x_out) of four values each."""
+    info = prob.amg_info()
+    n, nnz = info["nodes"][0], info["nnz"][0]
+    t = 8 if precision == "fp64" else 4
+    return nnz * (4 + 4 * t) + n * 4 * t * 6
+
+
+def measure(prob, torch, steps, rtol, kernel_class=None):
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    from paper_2403_04491_gb300.knp import launch_count
+    iters = []
+    if kernel_class is not None:
+        prob.profile_begin(kernel_class)
+    l0 = launch_count()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        iters.append(prob.step(1, rtol=rtol)[0]["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = launch_count() - l0
+    prof = prob.profile_end() if kernel_class is not None else None
+    return e0.elapsed_time(e1), iters, launches, prof
+
+
+def ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2403_04491_gb300 import problem_from_config
+    from synth import make_config
+
+    cfg = make_config(2)
+    prec = 0 if args.precision == "fp64" else 1
+    t0 = time.perf_counter()
+    mesh, prob = problem_from_config(cfg)
+    t_create = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prob.amg_setup(precision=prec)
+    t_amg = time.perf_counter() - t0
+    n_dof = prob.n_dof
+    for _ in range(args.warmup):
+        prob.step(1, rtol=args.rtol)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms, iters, launches, prof = measure(prob, torch, args.steps, args.rtol, kernel_class=1)
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_dof * args.steps * world / (ms / 1e3)
+
+    # end to end through the public API with host buffers: per step the state goes host->device,
+    # one knp_step runs, and the new state comes back device->host (pinned host memory)
+    st = prob.state_get()
+    host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in ("c_i", "phi_i", "c_e", "phi_e", "w")}
+    dev = {k: torch.empty(v.shape, dtype=torch.float64, device="cuda") for k, v in host.items()}
+    h2d = sum(v.numel() * 8 for v in host.values())
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    from paper_2403_04491_gb300 import knp as K
+    import ctypes as C
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for k in host:
+            dev[k].copy_(host[k], non_blocking=True)
+        ptr = lambda tt: C.cast(C.c_void_p(tt.data_ptr()), K._DP)
+        K._check(K._lib.knp_state_set(prob.handle, K.KNP_DEVICE, ptr(dev["c_i"]), ptr(dev["phi_i"]), ptr(dev["c_e"]),
+                                      ptr(dev["phi_e"]), ptr(dev["w"]), float(st["t"])))
+        prob.step(1, rtol=args.rtol)
+        tt = C.c_double()
+        K._check(K._lib.knp_state_get(prob.handle, K.KNP_DEVICE, ptr(dev["c_i"]), ptr(dev["phi_i"]), ptr(dev["c_e"]),
+                                      ptr(dev["phi_e"]), ptr(dev["w"]), C.byref(tt)))
+        st["t"] = tt.value
+        for k in host:
+            host[k].copy_(dev[k], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = n_dof * args.steps * world / (e2e_ms / 1e3)
+
+    # mixed-precision form (FP32 hierarchy and V-cycle under FP64 FGMRES), same workload
+    mixed = None
+    if not args.no_mixed and args.precision == "fp64":
+        out = {}
+        for rt in (1e-10, 1e-8):
+            _, pm = problem_from_config(cfg, mesh=mesh)
+            pm.amg_setup(precision=1)
+            for _ in range(args.warmup):
+                pm.step(1, rtol=rt)
+            msm, itm, _, _ = measure(pm, torch, args.steps, rt)
+            out[f"rtol_{rt:g}"] = dict(value=n_dof * args.steps / (msm / 1e3), iters_per_step=float(np.mean(itm)))
+            pm.close()
+        _, pf = problem_from_config(cfg, mesh=mesh)
+        pf.amg_setup(precision=0)
+        for _ in range(args.warmup):
+            pf.step(1, rtol=1e-8)
+        msf, itf, _, _ = measure(pf, torch, args.steps, 1e-8)
+        pf.close()
+        out["fp64_rtol_1e-08"] = dict(value=n_dof * args.steps / (msf / 1e3), iters_per_step=float(np.mean(itf)))
+        out["speedup_fp32_vs_fp64_at_rtol_1e-08"] = out["rtol_1e-08"]["value"] / out["fp64_rtol_1e-08"]["value"]
+        mixed = out
+
+    if rank != 0:
+        return
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    n_launch, prof_ms = prof
+    bytes_per = dominant_kernel_bytes(prob, args.precision)
+    achieved = bytes_per / (prof_ms / n_launch / 1e3) / 1e9 if n_launch else None
+    traffic = None
+    if os.path.exists(PROFILE_FILE):
+        pf = json.load(open(PROFILE_FILE))
+        ent = pf.get(f"cheb_fine_{args.precision}")
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            traffic = ent.get("dram_bytes_per_launch")
+    roof = dict(bound="hbm", kernel="k_cheb_sell (finest-level Chebyshev step of the V-cycle)",
+                achieved=achieved, peak=peak, unit="GB/s", frac=(achieved / peak) if achieved else None,
+                traffic=traffic, peak_source="measured" if "hbm_gbs" in peaks else "fallback",
+                algorithmic_bytes_per_launch=bytes_per, launches=n_launch,
+                avg_launch_us=1e3 * prof_ms / n_launch if n_launch else None,
+                share_of_step=prof_ms / ms if ms else None)
+    cpu = None
+    if not args.no_baseline and world == 1:
+        r = run_oracle(3, 1)
+        v = r["n_dof"] * len(r["times"]) / sum(r["times"])
+        cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=oracle_sample_desc(SAMPLE_NX, 3))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64" if args.precision == "fp64" else "f64 (FGMRES) / f32 (AMG)", data="synthetic",
+                config=dict(workload=WORKLOAD, n_dof=n_dof, l2="working set per step > L2 (operator, hierarchy and "
+                                                               "Krylov basis exceed 129 MB); no flush",
+                            precision=args.precision, rtol=args.rtol, restart=30,
+                            parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+                iters_per_step=float(np.mean(iters)), iters=iters, setup_s=dict(create=t_create, amg=t_amg),
+                amg=prob.amg_info(), gpu_launches=launches, clocks=clocks, roofline=roof,
+                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=h2d),
+                cpu_baseline=cpu, mixed=mixed)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

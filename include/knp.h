@@ -148,6 +148,8 @@ typedef struct {
     int32_t max_levels;
     int32_t cheb_degree;        /* Chebyshev smoothing degree (pre and post) */
     double cheb_ratio;          /* lower eigenvalue bound = lambda_max / cheb_ratio */
+    double theta_coarse;        /* strength threshold on levels >= 1 (< 0: same as theta) */
+    double p_drop;              /* drop prolongator entries below p_drop x the row's largest (0: keep all) */
 } knp_amg_opts;
 
 /* Smoothed-aggregation AMG on P_0 (Eq. 4.3) assembled from the initial
@@ -219,6 +221,30 @@ knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* 
  * length >= max_levels), operator complexity. */
 knp_status knp_amg_info(const knp_problem* prob, int32_t* levels, int64_t* nodes, int64_t* nnz,
                         double* op_complexity);
+
+typedef struct {
+    int64_t n_nodes;          /* N_i + N_e */
+    int64_t nnz_region;       /* stored same-region node-block entries of A (no padding) */
+    int64_t nnz_padded;       /* the same in the sliced-ELL layout, with padding */
+    int64_t nnz_cross;        /* cross-region membrane entries (B_rq) */
+    int64_t n_membrane_pairs; /* membrane vertex pairs sharing a facet */
+    int64_t n_edges;          /* undirected same-region edges */
+    int64_t edge_incidences;  /* (edge, element) incidences used by the weighted-stiffness pass */
+    int64_t step_index;       /* committed steps */
+} knp_problem_info;
+knp_status knp_problem_get_info(const knp_problem* prob, knp_problem_info* info);
+
+/* Kernel timing for roofline measurements: while a class is active, the library
+ * records a CUDA event pair on the problem's stream around every launch of that
+ * class. knp_profile_end synchronises the stream and returns the launch count and
+ * the summed device time. Classes: 0 operator SpMV (y = A x), 1 finest-level
+ * Chebyshev step, 2 finest-level residual, 3 assembly (the six kernels of one
+ * knp_assemble_step as one interval), 4 whole V-cycle, 5 Arnoldi orthogonalisation
+ * (one iteration's kernels as one interval). */
+knp_status knp_profile_begin(knp_problem* prob, int32_t kernel_class);
+knp_status knp_profile_end(knp_problem* prob, int64_t* launches, double* total_ms);
+/* Number of CUDA kernels this library has launched since it was loaded. */
+knp_status knp_launch_count(int64_t* count);
 
 const char* knp_last_error(void);
 

@@ -42,6 +42,8 @@ struct AmgSetupOpts {
     int coarse_max;
     int max_levels;
     double cheb_ratio;
+    double theta_coarse;
+    double p_drop;
 };
 
 // Builds the hierarchy from the fine operator (field values) and the fine

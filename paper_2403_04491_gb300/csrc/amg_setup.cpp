@@ -287,7 +287,7 @@ void amg_build(const HostCsr4& A0, const std::vector<double>& strength0, int64_t
         finish_level(L, o.cheb_ratio);
         const int64_t n = L.A.n_rows;
         if (n <= o.coarse_max || lev + 1 >= o.max_levels) break;
-        Graph G = strength_graph(L.A, strength, o.theta);
+        Graph G = strength_graph(L.A, strength, lev == 0 || o.theta_coarse < 0 ? o.theta : o.theta_coarse);
         std::vector<int32_t> agg;
         int64_t na = mis2_aggregate(G, n, lev, agg);
         if (na >= n || na == 0 || (double)na > 0.85 * (double)n) break;
@@ -323,7 +323,14 @@ void amg_build(const HostCsr4& A0, const std::vector<double>& strength0, int64_t
             std::vector<int32_t> order(cols.size());
             std::iota(order.begin(), order.end(), 0);
             std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cols[a] < cols[b]; });
+            double rmax[4] = {0, 0, 0, 0};
+            for (size_t q = 0; q < cols.size(); ++q)
+                for (int f = 0; f < 4; ++f) rmax[f] = std::max(rmax[f], std::fabs(acc[4 * q + f]));
             for (int32_t oo : order) {
+                // keep an entry if it is significant in any field (the pattern is shared)
+                bool keep = cols[oo] == agg[i] || o.p_drop <= 0;
+                for (int f = 0; f < 4 && !keep; ++f) keep = std::fabs(acc[4 * oo + f]) >= o.p_drop * rmax[f];
+                if (!keep) continue;
                 P.col.push_back(cols[oo]);
                 for (int f = 0; f < 4; ++f) P.val.push_back(acc[4 * oo + f]);
             }

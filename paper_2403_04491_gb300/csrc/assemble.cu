@@ -255,6 +255,8 @@ void launch_assembly(knp_problem* P) {
     sp.g_stim = stimulus_at(P->desc, P->t);
     const int64_t n = P->n_nodes, nmv = P->n_mv;
     const int nvpe = P->dim + 1;
+    ProfScope ps(&P->prof, KC_ASSEMBLY, st);
+    count_launch(2 + (nmv ? 2 : 0) + (P->n_edges ? 1 : 0) + (P->n_pairs ? 1 : 0));
     if (nmv) k_membrane_nodes<<<nblk(nmv, 128), 128, 0, st>>>(sp, nmv, P->mv_g.p, P->u.p, P->gates.p, P->gates_new.p,
                                                          P->mfield.p);
     k_elem_means<<<nblk(P->n_elem), 256, 0, st>>>(P->n_elem, nvpe, P->el_nodes.p, P->u.p, P->cbar.p);

@@ -130,7 +130,8 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
         KNP_REQUIRE(o->precision == KNP_PREC_FP64 || o->precision == KNP_PREC_FP32, KNP_ERR_INVALID_ARG,
                     "unknown precision");
         KNP_REQUIRE(o->theta >= 0 && o->theta < 1 && o->coarse_max >= 1 && o->max_levels >= 1 &&
-                        o->cheb_degree >= 1 && o->cheb_degree <= 8 && o->cheb_ratio > 1,
+                        o->cheb_degree >= 1 && o->cheb_degree <= 8 && o->cheb_ratio > 1 && o->theta_coarse < 1 &&
+                        o->p_drop >= 0 && o->p_drop < 1,
                     KNP_ERR_INVALID_ARG, "AMG options out of range");
         if (!p->assembled) launch_assembly(p);
         cudaStream_t st = p->stream;
@@ -181,7 +182,7 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
             si[i] = 1.0 / sv[i];
         }
         HostHierarchy H;
-        AmgSetupOpts so{o->theta, o->coarse_max, o->max_levels, o->cheb_ratio};
+        AmgSetupOpts so{o->theta, o->coarse_max, o->max_levels, o->cheb_ratio, o->theta_coarse, o->p_drop};
         amg_build(A0, strength, p->pin, so, H);
         amg_upload(p, H, o->precision, o->cheb_degree);
         KNP_CUDA(cudaMemcpyAsync(p->svec.p, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice, st));

@@ -196,6 +196,7 @@ void gmres_free(GmresWork* g) { delete g; }
 
 // squared norm of a device vector (through the multi-dot kernels)
 static double norm2_dev(GmresWork& g, const double* v, cudaStream_t st) {
+    count_launch(2);
     k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(g.n4, nullptr, 0, 0, v, nullptr, g.partial.p);
     k_reduce<<<1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 1, g.dots.p);
     double s;
@@ -214,6 +215,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     const unsigned nb = (unsigned)((n4 + 255) / 256);
     double* x = p->u.p;
     // reference norms ||S x_0|| of the stopping test, concentrations and potentials apart
+    count_launch(3);
     k_mdot_split<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, 0, x, p->svec.p, g.partial.p);
     k_reduce<<<2, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2, g.dots.p + 2 * MAXV);
     double xn2[2];
@@ -221,6 +223,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     KNP_CUDA(cudaStreamSynchronize(st));
     KNP_REQUIRE(std::isfinite(xn2[0]) && std::isfinite(xn2[1]), KNP_ERR_NUMERIC, "initial guess is not finite");
     k_scale_copy<<<nb, 256, 0, st>>>(n4, p->f.p, p->sinv.p, g.tmp.p);
+    count_launch();
     const double bnorm = std::sqrt(norm2_dev(g, g.tmp.p, st));
     KNP_REQUIRE(std::isfinite(bnorm), KNP_ERR_NUMERIC, "right-hand side is not finite");
     knp_status_detail res{KNP_OK, 0, 0, 0.0};
@@ -242,6 +245,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         }
         if (its >= o.max_it) break;
         if (its > 0) restarts++;
+        count_launch();
         k_scale_inplace<<<nb, 256, 0, st>>>(n4, g.V.p, 1.0 / beta);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
@@ -251,6 +255,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
             double* zj = g.Z.p + (int64_t)j * n4;
             // z_j = V-cycle(S v_j); row j of the S^2-weighted Gram matrices of Z (two field groups)
             vcycle_apply(p, vj, p->svec.p, zj);
+            count_launch(2);
             k_mdot_split<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.Z.p, n4, j, zj, p->svec.p, g.partial.p);
             k_reduce<<<2 * j + 2, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2 * j + 2, g.dots.p + 2 * MAXV);
             const bool arnoldi = (j < m) && (its < o.max_it);
@@ -258,6 +263,8 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
             if (arnoldi) {
                 double* w = g.V.p + (int64_t)(j + 1) * n4;
                 op_apply(p, zj, w, p->sinv.p, nullptr);
+                ProfScope ps(&p->prof, KC_ORTHO, st);
+                count_launch(5);
                 k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, w, nullptr, g.partial.p);
                 k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p);
                 k_orth_update_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, g.dots.p, w, g.partial.p);
@@ -337,6 +344,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                 y[k] = s / H[k * m + k];
             }
             KNP_CUDA(cudaMemcpyAsync(g.y.p, y.data(), k_done * sizeof(double), cudaMemcpyHostToDevice, st));
+            count_launch();
             k_update_x<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.Z.p, n4, k_done, g.y.p, x);
             KNP_CUDA(cudaGetLastError());
         }

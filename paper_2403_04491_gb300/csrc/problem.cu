@@ -270,6 +270,7 @@ void build_problem(knp_problem* P) {
             }
     }
     for (int64_t i = 0; i < n_edges; ++i) e_cnt[i + 1] += e_cnt[i];
+    P->n_edge_inc = e_cnt[n_edges];
     std::vector<int32_t> h_einc(e_cnt[n_edges]);
     std::vector<double> h_ecoef(e_cnt[n_edges]);
     {
@@ -407,6 +408,7 @@ void build_problem(knp_problem* P) {
     P->sinv.alloc(4 * n);
     P->svec.alloc(4 * n);
     const knp_problem_desc& d = P->desc;
+    count_launch(nmv ? 2 : 1);
     k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
                                           d.c_e0[2], d.phi_M0);
     if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
@@ -422,6 +424,7 @@ void download_state(const knp_problem* p, std::vector<double>& u) {
 void state_copy_out(const knp_problem* p, bool device, double* c_i, double* phi_i, double* c_e, double* phi_e) {
     const int64_t Ni = p->N_i, Ne = p->N_e, n = Ni + Ne;
     if (device) {
+        count_launch();
         k_state_out<<<nblk(n), 256, 0, p->stream>>>(p->u.p, Ni, Ne, c_i, phi_i, c_e, phi_e);
         KNP_CUDA(cudaGetLastError());
         KNP_CUDA(cudaStreamSynchronize(p->stream));
@@ -447,6 +450,7 @@ void state_copy_in(knp_problem* p, bool device, const double* c_i, const double*
                    const double* phi_e) {
     const int64_t Ni = p->N_i, Ne = p->N_e, n = Ni + Ne;
     if (device) {
+        count_launch();
         k_state_in<<<nblk(n), 256, 0, p->stream>>>(p->u.p, Ni, Ne, c_i, phi_i, c_e, phi_e);
         KNP_CUDA(cudaGetLastError());
         return;

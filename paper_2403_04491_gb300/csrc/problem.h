@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.h"
+#include "profile.h"
 
 namespace knp {
 
@@ -96,7 +97,7 @@ struct knp_problem {
     std::vector<double> facet_gleak;
     std::vector<uint8_t> stim_mask;
     int32_t dim = 0;
-    int64_t N_i = 0, N_e = 0, n_nodes = 0, n_mv = 0, nf = 0, n_elem = 0, n_edges = 0, n_pairs = 0;
+    int64_t N_i = 0, N_e = 0, n_nodes = 0, n_mv = 0, nf = 0, n_elem = 0, n_edges = 0, n_pairs = 0, n_edge_inc = 0;
     int32_t pin = -1;               // global node of the pinned phi_e
     double t = 0.0;
     int64_t step_index = 0;
@@ -138,6 +139,7 @@ struct knp_problem {
     knp::DArray<double> sinv;            // 1/sqrt(diag P_0) (set by knp_amg_setup)
     knp::DArray<double> svec;            // sqrt(diag P_0)
 
+    knp::Profiler prof;
     knp::AmgHierarchy* amg = nullptr;
     knp::GmresWork* gw = nullptr;
     ~knp_problem();

@@ -101,6 +101,8 @@ void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale
         for (int k = 0; k < KI; ++k) A.tau[r][k] = p->sp.reg[r].tau[k];
     for (int k = 0; k < KI; ++k) A.z[k] = p->sp.z[k];
     unsigned blocks = (unsigned)((A.n + 127) / 128);
+    ProfScope ps(&p->prof, KC_SPMV, p->stream);
+    count_launch();
     k_op_apply<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
     KNP_CUDA(cudaGetLastError());
 }

@@ -3,6 +3,11 @@
 // Chebyshev smoothing, all four fields of a node in one pass). Templated on the
 // storage/arithmetic type of the hierarchy: double (plain FP64 form) or float (the
 // mixed-precision form; the coarsest dense solve is FP64 in both).
+//
+// Layouts: the finest operator (about 15 entries per row in 3D) is sliced-ELL with one
+// thread per row; coarser operators and the transfer operators are CSR processed by
+// groups of TPR threads per row (TPR a power of two chosen from the mean row length),
+// so that the short, wide coarse levels still fill the GPU.
 #include <cmath>
 
 #include "amg.h"
@@ -42,11 +47,10 @@ struct V4<float> {
 };
 
 struct Coef4 {
-    float dummy;
     double c1[4], c2[4];
 };
 
-// acc = (A x)_row over the sliced-ELL row
+// Row product of a sliced-ELL operator (one thread per row)
 template <class T>
 __device__ __forceinline__ void sell_row(int64_t r, const int64_t* __restrict__ sp, const int32_t* __restrict__ col,
                                          const T* __restrict__ val, const T* __restrict__ x, T acc[4]) {
@@ -60,6 +64,24 @@ __device__ __forceinline__ void sell_row(int64_t r, const int64_t* __restrict__ 
         V4<T> xv = V4<T>::load(x + 4 * (int64_t)col[pos]);
         for (int f = 0; f < 4; ++f) acc[f] += a.v[f] * xv.v[f];
     }
+}
+
+// Row product of a CSR operator by a group of TPR lanes; every lane of the group gets the sum.
+// Every lane of the warp must call this (the shuffles use the full mask); rows r >= n pass
+// active = false and contribute nothing.
+template <class T, int TPR>
+__device__ __forceinline__ void csr_row(bool active, int64_t r, int lane, const int64_t* __restrict__ ptr,
+                                        const int32_t* __restrict__ col, const T* __restrict__ val,
+                                        const T* __restrict__ x, T acc[4]) {
+    acc[0] = acc[1] = acc[2] = acc[3] = T(0);
+    const int64_t t0 = active ? ptr[r] + lane : 0, t1 = active ? ptr[r + 1] : 0;
+    for (int64_t t = t0; t < t1; t += TPR) {
+        V4<T> a = V4<T>::load(val + 4 * t);
+        V4<T> xv = V4<T>::load(x + 4 * (int64_t)col[t]);
+        for (int f = 0; f < 4; ++f) acc[f] += a.v[f] * xv.v[f];
+    }
+    for (int o = TPR / 2; o > 0; o >>= 1)
+        for (int f = 0; f < 4; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o, TPR);
 }
 
 // first Chebyshev step from x = 0: d = c2 D^-1 b, x = d. On the finest level b = s .* v (double input).
@@ -81,17 +103,11 @@ __global__ void k_cheb_first(int64_t n, const double* __restrict__ v, const doub
     dd.store(x + 4 * i);
 }
 
-// Chebyshev step: r = b - A x_in; d = c1 d + c2 D^-1 r; x_out = x_in + d
+// Chebyshev update of one row given acc = (A x_in)_row
 template <class T>
-__global__ void __launch_bounds__(128) k_cheb_step(int64_t n, const int64_t* __restrict__ sp,
-                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                   const T* __restrict__ x_in, const T* __restrict__ b,
-                                                   const T* __restrict__ dinv, Coef4 c, T* __restrict__ d,
-                                                   T* __restrict__ x_out) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T acc[4];
-    sell_row<T>(i, sp, col, val, x_in, acc);
+__device__ __forceinline__ void cheb_update(int64_t i, const T acc[4], const T* __restrict__ x_in,
+                                            const T* __restrict__ b, const T* __restrict__ dinv, const Coef4& c,
+                                            T* __restrict__ d, T* __restrict__ x_out) {
     V4<T> bb = V4<T>::load(b + 4 * i), di = V4<T>::load(dinv + 4 * i), dd = V4<T>::load(d + 4 * i),
           xx = V4<T>::load(x_in + 4 * i);
     for (int f = 0; f < 4; ++f) {
@@ -102,10 +118,39 @@ __global__ void __launch_bounds__(128) k_cheb_step(int64_t n, const int64_t* __r
     xx.store(x_out + 4 * i);
 }
 
+// Chebyshev step: r = b - A x_in; d = c1 d + c2 D^-1 r; x_out = x_in + d
 template <class T>
-__global__ void __launch_bounds__(128) k_residual(int64_t n, const int64_t* __restrict__ sp,
+__global__ void __launch_bounds__(128) k_cheb_sell(int64_t n, const int64_t* __restrict__ sp,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ x_in, const T* __restrict__ b,
+                                                   const T* __restrict__ dinv, Coef4 c, T* __restrict__ d,
+                                                   T* __restrict__ x_out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T acc[4];
+    sell_row<T>(i, sp, col, val, x_in, acc);
+    cheb_update<T>(i, acc, x_in, b, dinv, c, d, x_out);
+}
+
+template <class T, int TPR>
+__global__ void __launch_bounds__(128) k_cheb_csr(int64_t n, const int64_t* __restrict__ ptr,
                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                  const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
+                                                  const T* __restrict__ x_in, const T* __restrict__ b,
+                                                  const T* __restrict__ dinv, Coef4 c, T* __restrict__ d,
+                                                  T* __restrict__ x_out) {
+    int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    int64_t i = g / TPR;
+    int lane = (int)(g % TPR);
+    T acc[4];
+    csr_row<T, TPR>(i < n, i, lane, ptr, col, val, x_in, acc);
+    if (lane == 0 && i < n) cheb_update<T>(i, acc, x_in, b, dinv, c, d, x_out);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_resid_sell(int64_t n, const int64_t* __restrict__ sp,
+                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                    const T* __restrict__ x, const T* __restrict__ b,
+                                                    T* __restrict__ r) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     T acc[4];
@@ -115,26 +160,43 @@ __global__ void __launch_bounds__(128) k_residual(int64_t n, const int64_t* __re
     bb.store(r + 4 * i);
 }
 
-// y[i] (+)= sum_t M(i, col[t]) x[col[t]] for a CSR with four values per entry
-template <class T>
-__global__ void k_csr4(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                       const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int accumulate) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T acc[4] = {0, 0, 0, 0};
-    for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
-        V4<T> a = V4<T>::load(val + 4 * t);
-        V4<T> xv = V4<T>::load(x + 4 * (int64_t)col[t]);
-        for (int f = 0; f < 4; ++f) acc[f] += a.v[f] * xv.v[f];
+template <class T, int TPR>
+__global__ void __launch_bounds__(128) k_resid_csr(int64_t n, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ x, const T* __restrict__ b,
+                                                   T* __restrict__ r) {
+    int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    int64_t i = g / TPR;
+    int lane = (int)(g % TPR);
+    T acc[4];
+    csr_row<T, TPR>(i < n, i, lane, ptr, col, val, x, acc);
+    if (lane == 0 && i < n) {
+        V4<T> bb = V4<T>::load(b + 4 * i);
+        for (int f = 0; f < 4; ++f) bb.v[f] -= acc[f];
+        bb.store(r + 4 * i);
     }
-    V4<T> yy;
-    if (accumulate) {
-        yy = V4<T>::load(y + 4 * i);
-        for (int f = 0; f < 4; ++f) yy.v[f] += acc[f];
-    } else {
-        for (int f = 0; f < 4; ++f) yy.v[f] = acc[f];
+}
+
+// y[i] (+)= (M x)[i] for a CSR with four values per entry (restriction and prolongation)
+template <class T, int TPR>
+__global__ void __launch_bounds__(128) k_csr4(int64_t n, const int64_t* __restrict__ ptr,
+                                              const int32_t* __restrict__ col, const T* __restrict__ val,
+                                              const T* __restrict__ x, T* __restrict__ y, int accumulate) {
+    int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    int64_t i = g / TPR;
+    int lane = (int)(g % TPR);
+    T acc[4];
+    csr_row<T, TPR>(i < n, i, lane, ptr, col, val, x, acc);
+    if (lane == 0 && i < n) {
+        V4<T> yy;
+        if (accumulate) {
+            yy = V4<T>::load(y + 4 * i);
+            for (int f = 0; f < 4; ++f) yy.v[f] += acc[f];
+        } else {
+            for (int f = 0; f < 4; ++f) yy.v[f] = acc[f];
+        }
+        yy.store(y + 4 * i);
     }
-    yy.store(y + 4 * i);
 }
 
 // x_f = Ainv_f b_f on the coarsest level, FP64; one warp per (field, row)
@@ -165,21 +227,44 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
+int pick_tpr(double mean_len) {
+    int t = 1;
+    while (t < 32 && t * 2 <= mean_len) t *= 2;
+    return t;
+}
+
 }  // namespace
 
 template <class T>
-struct DevLevel {
-    int64_t n = 0, nnz_pad = 0;
-    DArray<int64_t> sp;
+struct DevCsr4 {
+    int64_t n = 0;
+    int tpr = 1;
+    DArray<int64_t> ptr;
     DArray<int32_t> col;
     DArray<T> val;
+    void upload(const HostCsr4& h, cudaStream_t st) {
+        n = h.n_rows;
+        tpr = pick_tpr(n ? (double)h.nnz() / (double)n : 1.0);
+        ptr.upload(h.ptr, st);
+        col.upload(h.col, st);
+        val.upload(cast_vec<T>(h.val), st);
+    }
+};
+
+template <class T>
+struct DevLevel {
+    int64_t n = 0, nnz = 0;
+    bool sell = false;
+    // sliced ELL (finest level)
+    DArray<int64_t> sp;
+    DArray<int32_t> scol;
+    DArray<T> sval;
+    // CSR (coarser levels)
+    DevCsr4<T> A;
     DArray<T> dinv;
     double lmax[4], lmin[4];
-    DArray<int64_t> Pptr, Rptr;
-    DArray<int32_t> Pcol, Rcol;
-    DArray<T> Pval, Rval;
+    DevCsr4<T> P, R;
     DArray<T> x, x2, b, r, d;
-    int64_t nnz_csr = 0;
 };
 
 template <class T>
@@ -197,75 +282,79 @@ AmgHierarchy::~AmgHierarchy() {
 }
 
 template <class T>
-static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, cudaStream_t st) {
-    D.degree = degree;
-    for (const HostLevel& HL : H.levels) {
-        auto L = std::make_unique<DevLevel<T>>();
-        const int64_t n = HL.A.n_rows;
-        L->n = n;
-        // CSR -> sliced ELL
-        int64_t ns = (n + SELL_C - 1) / SELL_C;
-        std::vector<int64_t> sp(ns + 1, 0);
-        for (int64_t s = 0; s < ns; ++s) {
-            int64_t w = 0;
-            for (int64_t r = s * SELL_C; r < std::min(n, (s + 1) * SELL_C); ++r) w = std::max(w, HL.A.ptr[r + 1] - HL.A.ptr[r]);
-            sp[s + 1] = sp[s] + w * SELL_C;
-        }
-        std::vector<int32_t> col(sp[ns]);
-        std::vector<T> val(4 * sp[ns], T(0));
-        for (int64_t s = 0; s < ns; ++s) {
-            int64_t w = (sp[s + 1] - sp[s]) / SELL_C;
-            for (int64_t lane = 0; lane < SELL_C; ++lane) {
-                int64_t r = s * SELL_C + lane;
-                int64_t len = r < n ? HL.A.ptr[r + 1] - HL.A.ptr[r] : 0;
-                for (int64_t k = 0; k < w; ++k) {
-                    int64_t pos = sp[s] + k * SELL_C + lane;
-                    if (k < len) {
-                        int64_t t = HL.A.ptr[r] + k;
-                        col[pos] = HL.A.col[t];
-                        for (int f = 0; f < 4; ++f) val[4 * pos + f] = (T)HL.A.val[4 * t + f];
-                    } else {
-                        col[pos] = (int32_t)std::min<int64_t>(r, n - 1);
-                    }
+static void upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
+    const int64_t n = A.n_rows;
+    int64_t ns = (n + SELL_C - 1) / SELL_C;
+    std::vector<int64_t> sp(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t w = 0;
+        for (int64_t r = s * SELL_C; r < std::min(n, (s + 1) * SELL_C); ++r) w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
+        sp[s + 1] = sp[s] + w * SELL_C;
+    }
+    std::vector<int32_t> col(sp[ns]);
+    std::vector<T> val(4 * sp[ns], T(0));
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t w = (sp[s + 1] - sp[s]) / SELL_C;
+        for (int64_t lane = 0; lane < SELL_C; ++lane) {
+            int64_t r = s * SELL_C + lane;
+            int64_t len = r < n ? A.ptr[r + 1] - A.ptr[r] : 0;
+            for (int64_t k = 0; k < w; ++k) {
+                int64_t pos = sp[s] + k * SELL_C + lane;
+                if (k < len) {
+                    int64_t t = A.ptr[r] + k;
+                    col[pos] = A.col[t];
+                    for (int f = 0; f < 4; ++f) val[4 * pos + f] = (T)A.val[4 * t + f];
+                } else {
+                    col[pos] = (int32_t)std::min<int64_t>(r, n - 1);
                 }
             }
         }
-        L->nnz_pad = sp[ns];
-        L->nnz_csr = HL.A.nnz();
-        L->sp.upload(sp, st);
-        L->col.upload(col, st);
-        L->val.upload(val, st);
+    }
+    L.sp.upload(sp, st);
+    L.scol.upload(col, st);
+    L.sval.upload(val, st);
+}
+
+template <class T>
+static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, cudaStream_t st) {
+    D.degree = degree;
+    for (size_t l = 0; l < H.levels.size(); ++l) {
+        const HostLevel& HL = H.levels[l];
+        auto L = std::make_unique<DevLevel<T>>();
+        const int64_t n = HL.A.n_rows;
+        L->n = n;
+        L->nnz = HL.A.nnz();
+        L->sell = (double)L->nnz / (double)std::max<int64_t>(n, 1) <= 24.0;
+        if (L->sell)
+            upload_sell(*L, HL.A, st);
+        else
+            L->A.upload(HL.A, st);
         L->dinv.upload(cast_vec<T>(HL.dinv), st);
         for (int f = 0; f < 4; ++f) {
             L->lmax[f] = HL.lmax[f];
             L->lmin[f] = HL.lmin[f];
         }
         if (HL.P.n_rows) {
-            L->Pptr.upload(HL.P.ptr, st);
-            L->Pcol.upload(HL.P.col, st);
-            L->Pval.upload(cast_vec<T>(HL.P.val), st);
-            L->Rptr.upload(HL.R.ptr, st);
-            L->Rcol.upload(HL.R.col, st);
-            L->Rval.upload(cast_vec<T>(HL.R.val), st);
+            L->P.upload(HL.P, st);
+            L->R.upload(HL.R, st);
         }
         for (DArray<T>* v : {&L->x, &L->x2, &L->b, &L->r, &L->d}) {
             v->alloc(4 * n);
             v->zero(st);
         }
-        // Chebyshev coefficients
+        // Chebyshev coefficients of each step (Saad's three-term recurrence on [lmin, lmax])
         std::vector<Coef4> cs(std::max(degree, 1));
-        double rho0[4];
         for (int f = 0; f < 4; ++f) {
             double th = 0.5 * (L->lmax[f] + L->lmin[f]), de = 0.5 * (L->lmax[f] - L->lmin[f]);
             double sigma = th / de;
-            rho0[f] = 1.0 / sigma;
+            double rho0 = 1.0 / sigma;
             cs[0].c1[f] = 0.0;
             cs[0].c2[f] = 1.0 / th;
             for (int k = 1; k < degree; ++k) {
-                double rho1 = 1.0 / (2.0 * sigma - rho0[f]);
-                cs[k].c1[f] = rho1 * rho0[f];
+                double rho1 = 1.0 / (2.0 * sigma - rho0);
+                cs[k].c1[f] = rho1 * rho0;
                 cs[k].c2[f] = 2.0 * rho1 / de;
-                rho0[f] = rho1;
+                rho0 = rho1;
             }
         }
         D.coef.push_back(cs);
@@ -296,55 +385,97 @@ void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degre
     KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 
-template <class T>
-static void smooth(DevLevel<T>& L, const std::vector<Coef4>& cs, int degree, bool zero_start, const double* v,
-                   const double* s, cudaStream_t st) {
-    const unsigned nb = nblk(L.n, 128);
-    int k0 = 0;
-    if (zero_start) {
-        k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, cs[0], L.x.p, L.d.p);
-        k0 = 1;
+#define KNP_TPR_DISPATCH(tpr, KERNEL, grid_rows, ...)                                                      \
+    switch (tpr) {                                                                                         \
+        case 1: KERNEL<T, 1><<<nblk((grid_rows) * 1, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
+        case 2: KERNEL<T, 2><<<nblk((grid_rows) * 2, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
+        case 4: KERNEL<T, 4><<<nblk((grid_rows) * 4, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
+        case 8: KERNEL<T, 8><<<nblk((grid_rows) * 8, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
+        case 16: KERNEL<T, 16><<<nblk((grid_rows) * 16, 128), 128, 0, st>>>(__VA_ARGS__); break;          \
+        default: KERNEL<T, 32><<<nblk((grid_rows) * 32, 128), 128, 0, st>>>(__VA_ARGS__); break;          \
     }
-    for (int k = k0; k < degree; ++k) {
-        k_cheb_step<T><<<nb, 128, 0, st>>>(L.n, L.sp.p, L.col.p, L.val.p, L.x.p, L.b.p, L.dinv.p, cs[k], L.d.p,
-                                           L.x2.p);
-        std::swap(L.x.p, L.x2.p);
+
+template <class T>
+static void cheb_step(DevLevel<T>& L, const Coef4& c, Profiler* pr, bool fine, cudaStream_t st) {
+    count_launch();
+    if (L.sell) {
+        ProfScope ps(fine ? pr : nullptr, KC_CHEB_FINE, st);
+        k_cheb_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, L.x.p, L.b.p, L.dinv.p, c,
+                                                       L.d.p, L.x2.p);
+    } else {
+        ProfScope ps(fine ? pr : nullptr, KC_CHEB_FINE, st);
+        KNP_TPR_DISPATCH(L.A.tpr, k_cheb_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, L.x.p, L.b.p, L.dinv.p, c,
+                         L.d.p, L.x2.p);
+    }
+    std::swap(L.x.p, L.x2.p);
+}
+
+template <class T>
+static void residual(DevLevel<T>& L, Profiler* pr, bool fine, cudaStream_t st) {
+    count_launch();
+    ProfScope ps(fine ? pr : nullptr, KC_RESID_FINE, st);
+    if (L.sell) {
+        k_resid_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, L.x.p, L.b.p, L.r.p);
+    } else {
+        KNP_TPR_DISPATCH(L.A.tpr, k_resid_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, L.x.p, L.b.p, L.r.p);
     }
 }
 
 template <class T>
-static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, cudaStream_t st) {
+static void csr_apply(DevCsr4<T>& M, const T* x, T* y, int accumulate, cudaStream_t st) {
+    count_launch();
+    KNP_TPR_DISPATCH(M.tpr, k_csr4, M.n, M.n, M.ptr.p, M.col.p, M.val.p, x, y, accumulate);
+}
+
+template <class T>
+static void smooth(DevLevel<T>& L, const std::vector<Coef4>& cs, int degree, bool zero_start, const double* v,
+                   const double* s, Profiler* pr, bool fine, cudaStream_t st) {
+    int k0 = 0;
+    if (zero_start) {
+        count_launch();
+        k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, cs[0], L.x.p, L.d.p);
+        k0 = 1;
+    }
+    for (int k = k0; k < degree; ++k) cheb_step(L, cs[k], pr, fine, st);
+}
+
+template <class T>
+static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, Profiler* pr, cudaStream_t st) {
     DevLevel<T>& L = *D.L[l];
     const int last = (int)D.L.size() - 1;
     if (l == last) {
         if (v) {
             // single-level hierarchy: build b from the scaled input first
             Coef4 c0{};
+            count_launch();
             k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, c0, L.x.p, L.d.p);
         }
+        count_launch();
         k_coarse<T><<<nblk(4 * D.nc * 32, 256), 256, 0, st>>>(D.nc, D.cinv.p, L.b.p, L.x.p);
         return;
     }
     DevLevel<T>& C = *D.L[l + 1];
-    smooth(L, D.coef[l], D.degree, true, v, s, st);
-    k_residual<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.col.p, L.val.p, L.x.p, L.b.p, L.r.p);
-    k_csr4<T><<<nblk(C.n, 128), 128, 0, st>>>(C.n, L.Rptr.p, L.Rcol.p, L.Rval.p, L.r.p, C.b.p, 0);
-    vcycle_rec(D, l + 1, nullptr, nullptr, st);
-    k_csr4<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.Pptr.p, L.Pcol.p, L.Pval.p, C.x.p, L.x.p, 1);
-    smooth(L, D.coef[l], D.degree, false, nullptr, nullptr, st);
+    smooth(L, D.coef[l], D.degree, true, v, s, pr, l == 0, st);
+    residual(L, pr, l == 0, st);
+    csr_apply(L.R, L.r.p, C.b.p, 0, st);
+    vcycle_rec(D, l + 1, nullptr, nullptr, pr, st);
+    csr_apply(L.P, C.x.p, L.x.p, 1, st);
+    smooth(L, D.coef[l], D.degree, false, nullptr, nullptr, pr, l == 0, st);
 }
 
 // z = V-cycle(P_0)(s .* v); v, s, z are [n][4] doubles on the device.
 void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
     KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
     cudaStream_t st = p->stream;
+    ProfScope ps(&p->prof, KC_VCYCLE, st);
     if (p->amg->h32) {
         auto& D = *static_cast<AmgDev<float>*>(p->amg->h32);
-        vcycle_rec(D, 0, v, s, st);
+        vcycle_rec(D, 0, v, s, &p->prof, st);
+        count_launch();
         k_to_double<float><<<nblk(4 * D.L[0]->n, 256), 256, 0, st>>>(4 * D.L[0]->n, D.L[0]->x.p, z);
     } else {
         auto& D = *static_cast<AmgDev<double>*>(p->amg->h64);
-        vcycle_rec(D, 0, v, s, st);
+        vcycle_rec(D, 0, v, s, &p->prof, st);
         KNP_CUDA(cudaMemcpyAsync(z, D.L[0]->x.p, 4 * D.L[0]->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     KNP_CUDA(cudaGetLastError());

@@ -57,7 +57,8 @@ class ProblemDesc(C.Structure):
 
 class AmgOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("theta", C.c_double), ("coarse_max", C.c_int32),
-                ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("cheb_ratio", C.c_double)]
+                ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("cheb_ratio", C.c_double),
+                ("theta_coarse", C.c_double), ("p_drop", C.c_double)]
 
 
 class SolveOpts(C.Structure):
@@ -66,6 +67,12 @@ class SolveOpts(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("true_relres", C.c_double), ("ms", C.c_double)]
+
+
+class ProblemInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("nnz_region", C.c_int64), ("nnz_padded", C.c_int64),
+                ("nnz_cross", C.c_int64), ("n_membrane_pairs", C.c_int64), ("n_edges", C.c_int64),
+                ("edge_incidences", C.c_int64), ("step_index", C.c_int64)]
 
 
 class StepStats(C.Structure):
@@ -95,6 +102,10 @@ SIGNATURES = {
     "knp_operator_entries": [C.c_void_p, C.c_int64, _LP, _LP, _DP],
     "knp_apply_preconditioner": [C.c_void_p, _DP, _DP],
     "knp_amg_info": [C.c_void_p, _IP, _LP, _LP, _DP],
+    "knp_problem_get_info": [C.c_void_p, C.c_void_p],
+    "knp_profile_begin": [C.c_void_p, C.c_int32],
+    "knp_profile_end": [C.c_void_p, _LP, _DP],
+    "knp_launch_count": [_LP],
     "knp_last_error": [],
 }
 VOID_FUNCS = {"knp_mesh_destroy", "knp_problem_destroy"}
@@ -182,6 +193,12 @@ class Mesh:
             pass
 
 
+def launch_count():
+    n = C.c_int64()
+    _check(load_library().knp_launch_count(C.byref(n)))
+    return n.value
+
+
 def _current_stream():
     try:
         import torch
@@ -238,8 +255,8 @@ class Problem:
         _check(_lib.knp_assemble_step(self.handle))
 
     def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=2,
-                  cheb_ratio=10.0):
-        o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio)
+                  cheb_ratio=10.0, theta_coarse=0.0, p_drop=0.0):
+        o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop)
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
     def solve(self, rtol=1e-10, restart=30, max_it=1000):
@@ -312,6 +329,20 @@ class Problem:
         _check(_lib.knp_amg_info(self.handle, C.byref(lv), _lptr(nodes), _lptr(nnz), C.byref(oc)))
         return {"levels": lv.value, "nodes": nodes[:lv.value].tolist(), "nnz": nnz[:lv.value].tolist(),
                 "op_complexity": oc.value}
+
+    def info(self):
+        i = ProblemInfo()
+        _check(_lib.knp_problem_get_info(self.handle, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in ProblemInfo._fields_}
+
+    def profile_begin(self, kernel_class):
+        _check(_lib.knp_profile_begin(self.handle, int(kernel_class)))
+
+    def profile_end(self):
+        n = C.c_int64()
+        ms = C.c_double()
+        _check(_lib.knp_profile_end(self.handle, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
 
     def close(self):
         if getattr(self, "handle", None):
