@@ -217,6 +217,25 @@ knp_status knp_operator_entries(knp_problem* prob, int64_t count, const int64_t*
                                 const int64_t* cols, double* vals);
 /* z = V-cycle(P_0) r (one application of the preconditioner, unscaled); host [n]. */
 knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* z);
+/* Allocation-free variant of knp_apply_preconditioner. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc when they need the
+ * preconditioner - code running under a CUDA stream capture or while a CUDA graph is being
+ * built, hosts that fix their device memory up front, and plugin or embedded hosts that
+ * forbid allocation after start-up.
+ * r and z are DEVICE pointers to [n_dof] doubles in the same Eq. 4.2 order as
+ * knp_apply_preconditioner, owned by the caller; z = V-cycle(P_0) r with the same kernels
+ * and hierarchy, so the result equals knp_apply_preconditioner's. The call allocates
+ * nothing: its work vectors live in one static device array of 32 MiB that every GPU which
+ * loads the library holds until the process exits. Hierarchies whose work vectors need more
+ * than that (about 120,000 nodes with the FP64 hierarchy, 180,000 with FP32) are rejected with
+ * KNP_ERR_INVALID_ARG and a message giving the size. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls share the array and keep the last call's
+ * contents, so calls that overlap on the GPU (other streams, other problems, other host
+ * threads) race and must be serialised by the caller. Stream-ordered on the problem's
+ * stream; returns without synchronising. Errors: KNP_ERR_INVALID_ARG, KNP_ERR_STATE (no
+ * hierarchy), KNP_ERR_CUDA. */
+knp_status knp_apply_preconditioner_noalloc(knp_problem* prob, const double* r, double* z);
 /* Hierarchy summary: levels, per-level node counts and nonzeros (host arrays of
  * length >= max_levels), operator complexity. */
 knp_status knp_amg_info(const knp_problem* prob, int32_t* levels, int64_t* nodes, int64_t* nnz,

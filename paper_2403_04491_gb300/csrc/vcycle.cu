@@ -9,6 +9,8 @@
 // groups of TPR threads per row (TPR a power of two chosen from the mean row length),
 // so that the short, wide coarse levels still fill the GPU.
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "amg.h"
 #include "problem.h"
@@ -482,3 +484,193 @@ void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
 }
 
 }  // namespace knp
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of knp_apply_preconditioner (include/knp.h). Some callers cannot call
+// cudaMalloc when they need the preconditioner: code running under a CUDA stream capture or a
+// graph being built, callers whose memory is fixed up front by a host framework, and embedded or
+// plugin hosts that forbid allocation after start-up. The variant runs the same kernels as the
+// V-cycle above on the same hierarchy, but all of its work vectors (the per-level x, x', b, r, d,
+// the unit scale vector and the two layout-conversion buffers) live in one file-scope static
+// device array of KNP_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
+// the process exits. Calls share that array, so two calls that overlap on the GPU (different
+// streams, different problems, or different host threads) race on it and must be serialised.
+// Nothing in the array needs to start at zero: every work vector is written before it is read.
+// ---------------------------------------------------------------------------------------------
+
+namespace knp {
+
+namespace {
+
+constexpr size_t KNP_NOALLOC_SCRATCH_BYTES = size_t(32) << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KNP_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on the current device. Host code cannot use the symbol
+// itself (on the host it names a stand-in, not device memory), so the address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, and cached.
+std::mutex g_noalloc_mu;
+std::map<int, void*> g_noalloc_addr;
+
+unsigned char* noalloc_scratch() {
+    int dev = -1;
+    KNP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) return static_cast<unsigned char*>(it->second);
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    KNP_REQUIRE(e == cudaSuccess && ptr, KNP_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                cudaGetErrorString(e));
+    g_noalloc_addr[dev] = ptr;
+    return static_cast<unsigned char*>(ptr);
+}
+
+__global__ void k_fill(int64_t n, double v, double* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
+
+// Eq. 4.2 order [c_i^1..c_i^3, phi_i, c_e^1..c_e^3, phi_e] <-> node-major [node][4]
+__global__ void k_eq42_to_nodes(int64_t Ni, int64_t Ne, const double* __restrict__ a, double* __restrict__ out) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= Ni + Ne) return;
+    for (int k = 0; k < 4; ++k)
+        out[4 * g + k] = g < Ni ? a[(int64_t)k * Ni + g] : a[4 * Ni + (int64_t)k * Ne + (g - Ni)];
+}
+
+__global__ void k_nodes_to_eq42(int64_t Ni, int64_t Ne, const double* __restrict__ in, double* __restrict__ a) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= Ni + Ne) return;
+    for (int k = 0; k < 4; ++k) {
+        if (g < Ni)
+            a[(int64_t)k * Ni + g] = in[4 * g + k];
+        else
+            a[4 * Ni + (int64_t)k * Ne + (g - Ni)] = in[4 * g + k];
+    }
+}
+
+// per-level work vectors carved out of the static array
+template <class T>
+struct NaWork {
+    T *x, *x2, *b, *r, *d;
+};
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <class T>
+static void na_cheb_step(DevLevel<T>& L, NaWork<T>& w, const Coef4& c, cudaStream_t st) {
+    count_launch();
+    if (L.sell) {
+        k_cheb_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, w.x, w.b, L.dinv.p, c, w.d,
+                                                       w.x2);
+    } else {
+        KNP_TPR_DISPATCH(L.A.tpr, k_cheb_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, w.x, w.b, L.dinv.p, c, w.d,
+                         w.x2);
+    }
+    std::swap(w.x, w.x2);
+}
+
+template <class T>
+static void na_vcycle_rec(AmgDev<T>& D, std::vector<NaWork<T>>& W, int l, const double* v, const double* s,
+                          cudaStream_t st) {
+    DevLevel<T>& L = *D.L[l];
+    NaWork<T>& w = W[l];
+    const int last = (int)D.L.size() - 1;
+    if (l == last) {
+        if (v) {
+            Coef4 c0{};
+            count_launch();
+            k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, c0, w.x, w.d);
+        }
+        count_launch();
+        k_coarse<T><<<nblk(4 * D.nc * 32, 256), 256, 0, st>>>(D.nc, D.cinv.p, w.b, w.x);
+        return;
+    }
+    DevLevel<T>& C = *D.L[l + 1];
+    NaWork<T>& wc = W[l + 1];
+    const std::vector<Coef4>& cs = D.coef[l];
+    count_launch();
+    k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, cs[0], w.x, w.d);
+    for (int k = 1; k < D.degree; ++k) na_cheb_step(L, w, cs[k], st);
+    count_launch();
+    if (L.sell) {
+        k_resid_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, w.x, w.b, w.r);
+    } else {
+        KNP_TPR_DISPATCH(L.A.tpr, k_resid_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, w.x, w.b, w.r);
+    }
+    count_launch();
+    KNP_TPR_DISPATCH(L.R.tpr, k_csr4, C.n, C.n, L.R.ptr.p, L.R.col.p, L.R.val.p, w.r, wc.b, 0);
+    na_vcycle_rec(D, W, l + 1, nullptr, nullptr, st);
+    count_launch();
+    KNP_TPR_DISPATCH(L.P.tpr, k_csr4, L.n, L.n, L.P.ptr.p, L.P.col.p, L.P.val.p, wc.x, w.x, 1);
+    for (int k = 0; k < D.degree; ++k) na_cheb_step(L, w, cs[k], st);
+}
+
+// Lays the work vectors out in the static array; returns the bytes needed (and fills W when
+// `base` is not NULL).
+template <class T>
+static size_t na_layout(AmgDev<T>& D, int64_t n0, unsigned char* base, std::vector<NaWork<T>>& W, double** ones,
+                        double** rin, double** zout, T** xfine) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> unsigned char* {
+        unsigned char* p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    *ones = reinterpret_cast<double*>(take(4 * n0 * sizeof(double)));
+    *rin = reinterpret_cast<double*>(take(4 * n0 * sizeof(double)));
+    *zout = reinterpret_cast<double*>(take(4 * n0 * sizeof(double)));
+    W.assign(D.L.size(), NaWork<T>{});
+    for (size_t l = 0; l < D.L.size(); ++l) {
+        size_t b = 4 * (size_t)D.L[l]->n * sizeof(T);
+        W[l].x = reinterpret_cast<T*>(take(b));
+        W[l].x2 = reinterpret_cast<T*>(take(b));
+        W[l].b = reinterpret_cast<T*>(take(b));
+        W[l].r = reinterpret_cast<T*>(take(b));
+        W[l].d = reinterpret_cast<T*>(take(b));
+    }
+    *xfine = nullptr;
+    return off;
+}
+
+template <class T>
+static void na_apply(knp_problem* p, AmgDev<T>& D, const double* r_eq42, double* z_eq42) {
+    cudaStream_t st = p->stream;
+    const int64_t n0 = D.L[0]->n;
+    std::vector<NaWork<T>> W;
+    double *ones, *rin, *zout;
+    T* xf;
+    size_t need = na_layout(D, n0, nullptr, W, &ones, &rin, &zout, &xf);
+    KNP_REQUIRE(need <= KNP_NOALLOC_SCRATCH_BYTES, KNP_ERR_INVALID_ARG,
+                "knp_apply_preconditioner_noalloc needs %zu bytes of scratch for this hierarchy; the static "
+                "array holds %zu (use knp_apply_preconditioner)",
+                need, KNP_NOALLOC_SCRATCH_BYTES);
+    unsigned char* base = noalloc_scratch();
+    na_layout(D, n0, base, W, &ones, &rin, &zout, &xf);
+    count_launch(3);
+    k_fill<<<nblk(4 * n0, 256), 256, 0, st>>>(4 * n0, 1.0, ones);
+    k_eq42_to_nodes<<<nblk(n0, 256), 256, 0, st>>>(p->N_i, p->N_e, r_eq42, rin);
+    na_vcycle_rec(D, W, 0, rin, ones, st);
+    count_launch();
+    k_to_double<T><<<nblk(4 * n0, 256), 256, 0, st>>>(4 * n0, W[0].x, zout);
+    count_launch();
+    k_nodes_to_eq42<<<nblk(n0, 256), 256, 0, st>>>(p->N_i, p->N_e, zout, z_eq42);
+    KNP_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+}  // namespace knp
+
+extern "C" knp_status knp_apply_preconditioner_noalloc(knp_problem* p, const double* r, double* z) {
+    using namespace knp;
+    return guarded([&] {
+        KNP_REQUIRE(p && r && z, KNP_ERR_INVALID_ARG, "NULL argument");
+        KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
+        if (p->amg->h32)
+            na_apply(p, *static_cast<AmgDev<float>*>(p->amg->h32), r, z);
+        else
+            na_apply(p, *static_cast<AmgDev<double>*>(p->amg->h64), r, z);
+    });
+}
+

@@ -101,6 +101,7 @@ SIGNATURES = {
     "knp_apply_operator": [C.c_void_p, _DP, _DP],
     "knp_operator_entries": [C.c_void_p, C.c_int64, _LP, _LP, _DP],
     "knp_apply_preconditioner": [C.c_void_p, _DP, _DP],
+    "knp_apply_preconditioner_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p],
     "knp_amg_info": [C.c_void_p, _IP, _LP, _LP, _DP],
     "knp_problem_get_info": [C.c_void_p, C.c_void_p],
     "knp_profile_begin": [C.c_void_p, C.c_int32],
@@ -320,6 +321,12 @@ class Problem:
         z = np.empty(self.n_dof)
         _check(_lib.knp_apply_preconditioner(self.handle, _dptr(r), _dptr(z)))
         return z
+
+    def apply_preconditioner_noalloc(self, r_dev, z_dev):
+        """knp_apply_preconditioner_noalloc on device buffers (torch tensors or raw pointers) in the
+        same Eq. 4.2 order; allocates nothing (work vectors in the library's static device array)."""
+        ptr = lambda a: C.c_void_p(a if isinstance(a, int) else a.data_ptr())
+        _check(_lib.knp_apply_preconditioner_noalloc(self.handle, ptr(r_dev), ptr(z_dev)))
 
     def amg_info(self):
         lv = C.c_int32()
