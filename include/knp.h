@@ -159,12 +159,15 @@ typedef struct {
 knp_status knp_amg_setup(knp_problem* prob, const knp_amg_opts* opts);
 
 typedef struct {
-    double rtol;       /* on the preconditioned residual: ||S M^-1 r||_g <= rtol ||S u_{n-1}||_g for the
-                          concentration part and the potential part g, S^2 = diag(P_0), M^-1 = one
-                          V-cycle on P_0 (the paper's preconditioned test, Section 6.2, in the scaled
-                          norm and relative to the initial guess) */
+    double rtol;       /* on the preconditioned residual: ||S M^-1 r||_g <= rtol max(||S x_0||_g,
+                          ||S (x - x_0)||_g) for the concentration part and the potential part g,
+                          S^2 = diag(P_0), M^-1 = one V-cycle on P_0, x_0 = u_{n-1} (the paper's
+                          preconditioned test, Section 6.2, in the scaled norm, relative to the
+                          initial guess or, for a cold start, to the computed correction) */
     int32_t restart;   /* 30 (Section 6.2) */
     int32_t max_it;    /* total iterations */
+    int32_t phi_e_group;  /* 1: test the extracellular potentials as a third group (phi_e is some 1e-8
+                             of phi_i; a loss built on phi_e needs it resolved on its own scale) */
 } knp_solve_opts;
 
 typedef struct {
@@ -189,6 +192,40 @@ typedef struct {
 knp_status knp_step(knp_problem* prob, int32_t nsteps, const knp_solve_opts* opts,
                     knp_step_stats* per_step);
 
+/* Replaces the per-facet leak conductances g_leak^k ([n_facets * n_ions], facet order of
+ * knp_mesh_facets, ion-minor) from host or device memory; takes effect at the next assembly.
+ * (The gradient of knp_adjoint_get is with respect to these.) */
+knp_status knp_problem_set_facet_gleak(knp_problem* prob, knp_memspace space, const double* gleak);
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint (not in the paper: the discrete adjoint of the time loop)          */
+/* ------------------------------------------------------------------------- */
+/* For a loss L(u_1..u_N) the reverse sweep runs, for n = N..1,
+ *     A_{n-1}^T lambda_n = dL/du_n + rho_n
+ * where rho_n carries d/du_n of the later steps' explicit dependence on u_n (through
+ * A^{k,n}, alpha, C, E_k, phi_M^n in I_ch and f, and the HH gates), and accumulates the
+ * gradients with respect to the per-facet leak conductances, u_0 and w_0. The
+ * transposed solve is FGMRES with the same P_0 hierarchy (P_0 is symmetric, Section
+ * 4.2) and the same stopping test.
+ * knp_adjoint_begin zeroes the carried quantities and the accumulators (allocating the
+ * adjoint work arrays on first use). */
+knp_status knp_adjoint_begin(knp_problem* prob);
+/* One reverse step n. Precondition: the problem's state is (u_{n-1}, w_{n-1}, t_{n-1})
+ * (restore it with knp_state_set, e.g. from a checkpoint and a recomputed segment). u_n
+ * is the forward solution of step n and dLdu_n the loss's partial derivative with
+ * respect to u_n, both [n_dof] in the Eq. 4.2 order, in `space`. The call assembles
+ * A_{n-1}, solves for lambda_n, and updates the carried quantities and the gradient
+ * accumulators. The state itself is not changed. Errors: KNP_ERR_STATE (no
+ * knp_adjoint_begin or knp_amg_setup), KNP_ERR_NOT_CONVERGED, KNP_ERR_CUDA. */
+knp_status knp_adjoint_step(knp_problem* prob, knp_memspace space, const double* u_n, const double* dLdu_n,
+                            const knp_solve_opts* opts, knp_solve_stats* stats);
+/* After the step n = 1: dLdu0 [n_dof] (Eq. 4.2 order; the entries of c_i^k are the
+ * gradient with respect to the initial intracellular concentrations), dLdw0 [3 *
+ * n_membrane_vertices], grad_gleak [n_facets * n_ions], and the last lambda [n_dof].
+ * Any pointer may be NULL; buffers in `space`. */
+knp_status knp_adjoint_get(knp_problem* prob, knp_memspace space, double* dLdu0, double* dLdw0,
+                           double* grad_gleak, double* lambda);
+
 /* State access in region node order. Buffers are [n_ions * N_r] (ion-major)
  * for concentrations, [N_r] for potentials, [3 * n_membrane_vertices] (gate-
  * major n, m, h) for gates; any pointer may be NULL. `space` says where the
@@ -211,6 +248,8 @@ knp_status knp_state_set(knp_problem* prob, knp_memspace space, const double* c_
 knp_status knp_rhs_get(const knp_problem* prob, double* rhs);
 /* y = A_{n-1} x with the last assembled operator; x, y host [n]. */
 knp_status knp_apply_operator(knp_problem* prob, const double* x, double* y);
+/* y = A_{n-1}^T x with the last assembled operator; x, y host [n]. */
+knp_status knp_apply_operator_transpose(knp_problem* prob, const double* x, double* y);
 /* Entries of A_{n-1}: for each (row, col) pair in the Eq. 4.2 order, the value
  * (0 where the entry is outside the pattern). rows, cols, vals host [count]. */
 knp_status knp_operator_entries(knp_problem* prob, int64_t count, const int64_t* rows,

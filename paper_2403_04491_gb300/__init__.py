@@ -6,3 +6,4 @@ membrane update, assembly, AMG V-cycle and FGMRES runs in the library's CUDA ker
 from .knp import (  # noqa: F401
     KnpError, Mesh, Problem, load_library, problem_from_config, KNP_PREC_FP32, KNP_PREC_FP64,
 )
+from .autograd import KNPFunction, Simulation, probe_weights  # noqa: F401,E402

@@ -4,7 +4,7 @@
 //   elem_means       element means of [k]^{n-1} (exact weight of A_r^{k,n-1} for P1)
 //   edge_values      A_r^{k,n-1} on each undirected edge: sum over incident elements
 //   row_assemble     per row: tau~ A^k off-diagonals, the diagonal as minus the row sum,
-//                    the pinned column, and the bulk right-hand side M c^{k,n-1}
+//                    and the bulk right-hand side M c^{k,n-1}
 //   membrane_pairs   C_r^k-weighted membrane mass on same-region and cross-region entries
 //   membrane_rhs     -int g_r^k v and -int h_r w at membrane nodes
 #include "problem.h"
@@ -131,14 +131,14 @@ __global__ void k_row_assemble(StepParams sp, int64_t n, int64_t N_i, int32_t pi
             dpos = pos;
             continue;
         }
-        bool pinned = (c == pin);
         for (int i = 0; i < KI; ++i) {
             double v = rc.taut[i] * ak[i * n_edges + ed];
             sum[i] += v;
-            e[i * n_entries + pos] = pinned ? 0.0 : v;
+            e[i * n_entries + pos] = v;
         }
     }
-    for (int i = 0; i < KI; ++i) e[i * n_entries + dpos] = (r == pin) ? 0.0 : -sum[i];
+    // the pinned phi_e column is not zeroed here: the operator kernels ignore it (see spmv.cu)
+    for (int i = 0; i < KI; ++i) e[i * n_entries + dpos] = -sum[i];
     for (int i = 0; i < KI; ++i) f[4 * r + i] = fm[i];
     f[4 * r + 3] = 0.0;
 }
@@ -167,16 +167,10 @@ __global__ void k_membrane_pairs(int64_t npairs, int64_t nmv, int dim, int32_t p
         }
     }
     const int32_t* tg = tgt + 4 * t;
-    // columns: SELL (i) -> i-node of b, never pinned; SELL (e) and cross (i row) -> e-node of b
-    int64_t pk0 = mpf[mp_ptr[t]];
-    int64_t f0 = pk0 >> 4;
-    int sb0 = pk0 & 3;
-    int64_t b = fmv[f0 * dim + sb0];
-    bool e_col_pinned = (mv_g[nmv + b] == pin);
     for (int k = 0; k < KI; ++k) {
         e[k * n_entries + tg[0]] += vi[k];
-        if (!e_col_pinned) e[k * n_entries + tg[1]] += ve[k];
-        xe[k * n_cross + tg[2]] = e_col_pinned ? 0.0 : -vi[k];
+        e[k * n_entries + tg[1]] += ve[k];
+        xe[k * n_cross + tg[2]] = -vi[k];
         xe[k * n_cross + tg[3]] = -ve[k];
     }
 }

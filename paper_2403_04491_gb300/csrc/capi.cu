@@ -61,6 +61,7 @@ using namespace knp;
 knp_problem::~knp_problem() {
     delete amg;
     gmres_free(gw);
+    adjoint_free(adj);
 }
 
 extern "C" {
@@ -187,6 +188,11 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
         amg_upload(p, H, o->precision, o->cheb_degree);
         KNP_CUDA(cudaMemcpyAsync(p->svec.p, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         KNP_CUDA(cudaMemcpyAsync(p->sinv.p, si.data(), si.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        // the pinned row is an identity whose scale says nothing about the solution: leave it out
+        // of the norms of the stopping test
+        std::vector<double> sw = sv;
+        sw[4 * (int64_t)p->pin + 3] = 0.0;
+        KNP_CUDA(cudaMemcpyAsync(p->swt.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         KNP_CUDA(cudaStreamSynchronize(st));
     });
 }
@@ -199,7 +205,7 @@ knp_status knp_solve(knp_problem* p, const knp_solve_opts* o, knp_solve_stats* s
         KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_solve called before knp_amg_setup");
         KNP_REQUIRE(o->rtol > 0 && o->restart >= 1 && o->max_it >= 1, KNP_ERR_INVALID_ARG, "solve options out of range");
         knp_solve_stats s{};
-        det = fgmres(p, *o, s);
+        det = fgmres(p, *o, s, p->u.p, p->f.p, false);
         if (stats) *stats = s;
         if (det.code == KNP_OK) {
             // commit the step: gates w_n, t_n
@@ -325,6 +331,8 @@ knp_status knp_operator_entries(knp_problem* p, int64_t count, const int64_t* ro
             double v = 0.0;
             if (r == p->pin && kr == 3) {
                 v = (c == r && kc == 3) ? 1.0 : 0.0;
+            } else if (c == p->pin && kc == 3) {
+                v = 0.0;   // the pinned column
             } else if ((r < Ni) == (c < Ni)) {
                 int64_t s = r / SELL_C, base = S.h_slice_ptr[s] + r % SELL_C;
                 int64_t w = (S.h_slice_ptr[s + 1] - S.h_slice_ptr[s]) / SELL_C;
@@ -374,6 +382,60 @@ knp_status knp_apply_preconditioner(knp_problem* p, const double* r, double* z) 
         dz.download(zi, p->stream);
         KNP_CUDA(cudaStreamSynchronize(p->stream));
         from_interleaved(p, zi, z);
+    });
+}
+
+knp_status knp_problem_set_facet_gleak(knp_problem* p, knp_memspace space, const double* gleak) {
+    return guarded([&] {
+        KNP_REQUIRE(p && gleak, KNP_ERR_INVALID_ARG, "NULL argument");
+        const int64_t nf = p->nf;
+        if (nf == 0) return;
+        KNP_CUDA(cudaMemcpyAsync(p->f_gleak.p, gleak, nf * KI * sizeof(double),
+                                 space == KNP_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+        KNP_CUDA(cudaStreamSynchronize(p->stream));
+        p->assembled = false;
+    });
+}
+
+knp_status knp_adjoint_begin(knp_problem* p) {
+    return guarded([&] {
+        KNP_REQUIRE(p, KNP_ERR_INVALID_ARG, "NULL problem");
+        adjoint_begin(p);
+    });
+}
+
+knp_status knp_adjoint_step(knp_problem* p, knp_memspace space, const double* u_n, const double* dLdu_n,
+                            const knp_solve_opts* o, knp_solve_stats* stats) {
+    return guarded([&] {
+        KNP_REQUIRE(p && u_n && dLdu_n && o, KNP_ERR_INVALID_ARG, "NULL argument");
+        KNP_REQUIRE(o->rtol > 0 && o->restart >= 1 && o->max_it >= 1, KNP_ERR_INVALID_ARG, "solve options out of range");
+        knp_solve_stats s{};
+        adjoint_step(p, space == KNP_DEVICE, u_n, dLdu_n, *o, s);
+        if (stats) *stats = s;
+    });
+}
+
+knp_status knp_adjoint_get(knp_problem* p, knp_memspace space, double* dLdu0, double* dLdw0, double* grad_gleak,
+                           double* lambda) {
+    return guarded([&] {
+        KNP_REQUIRE(p, KNP_ERR_INVALID_ARG, "NULL problem");
+        adjoint_get(p, space == KNP_DEVICE, dLdu0, dLdw0, grad_gleak, lambda);
+    });
+}
+
+knp_status knp_apply_operator_transpose(knp_problem* p, const double* x, double* y) {
+    return guarded([&] {
+        KNP_REQUIRE(p && x && y, KNP_ERR_INVALID_ARG, "NULL argument");
+        KNP_REQUIRE(p->assembled, KNP_ERR_STATE, "no assembled step");
+        std::vector<double> xi, yi(4 * p->n_nodes);
+        to_interleaved(p, x, xi);
+        DArray<double> dx, dy;
+        dx.upload(xi, p->stream);
+        dy.alloc(xi.size());
+        op_apply(p, dx.p, dy.p, nullptr, nullptr, true);
+        dy.download(yi, p->stream);
+        KNP_CUDA(cudaStreamSynchronize(p->stream));
+        from_interleaved(p, yi, y);
     });
 }
 

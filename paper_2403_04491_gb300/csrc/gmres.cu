@@ -9,12 +9,14 @@
 // is classical Gram-Schmidt with one reorthogonalisation (CGS2) in three fused passes.
 //
 // Stopping test: the preconditioned residual, as in Section 6.2, measured in the scaled
-// norm and relative to the initial guess, for the concentrations and the potentials apart:
-// ||S M^-1 r_k||_g <= rtol ||S x_0||_g for g in {c, phi}. A residual norm
+// norm and relative to the initial guess (or, if that is smaller, to the correction of the
+// current cycle, which covers a cold start), for the concentrations and the potentials apart:
+// ||S M^-1 r_k||_g <= rtol max(||S x_0||_g, ||S (x_k - x_0)||_g) for g in {c, phi}. A residual norm
 // alone is blind to the per-cell constant of phi_i (the intracellular potential block is
 // singular up to the small membrane mass), while M^-1 r approximates the error. For the
 // FGMRES iterate, M^-1 r_k = Z_{k+1} c with c = Q_k^T g_k e_{k+1} from the Givens rotations,
-// so its S-norms follow from the S^2-weighted Gram matrices of Z, one row per iteration.
+// so its S-norms follow from the S^2-weighted Gram matrices of Z, one row per iteration
+// (and so do those of the correction Z y_k).
 // (Apart, because the scaled concentrations outweigh the scaled potentials by two orders.)
 // The host sees one Hessenberg column and one Gram row per iteration.
 #include <chrono>
@@ -31,79 +33,139 @@ namespace {
 constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int MAXV = 32;          // restart + 2
-constexpr int MAXW = 2 * MAXV;    // partial-sum slots per block
+constexpr int MAXW = 3 * MAXV;    // partial-sum slots per block
 
-template <int NV>
-__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double* __restrict__ partial) {
-    __shared__ double sh[RED_THREADS / 32][NV];
+// Every kernel below is instantiated for a compile-time vector count NV, so that the
+// accumulators and basis values stay in registers (a runtime count put them on the stack).
+template <int NT>
+__device__ __forceinline__ void block_reduce_store(const double (&acc)[NT], double* __restrict__ partial) {
+    __shared__ double sh[RED_THREADS / 32][NT];
     const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-    for (int k = 0; k < nv; ++k) {
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
         double v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) sh[wid][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < nv) {
+    if (threadIdx.x < NT) {
         double s = 0;
         for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[w][threadIdx.x];
         partial[(int64_t)blockIdx.x * MAXW + threadIdx.x] = s;
     }
 }
 
-// partial[b][k] = block b's share of <V_k, w>_s for k < nv, and of <w, w>_s at k = nv, where
-// <a, b>_s = sum_i s_i^2 a_i b_i (s = NULL: plain dot)
-__global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n4, const double* __restrict__ V, int64_t ldv, int nv,
-                                                      const double* __restrict__ w, const double* __restrict__ s,
-                                                      double* __restrict__ partial) {
-    double acc[MAXV];
-    for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
+// partial[b][k] = block b's share of <V_k, w> for k < NV, and of <w, w> at k = NV
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(int64_t n4, const double* __restrict__ V, int64_t ldv,
+                                                      const double* __restrict__ w, double* __restrict__ partial) {
+    double acc[NV + 1];
+#pragma unroll
+    for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         double wi = w[i];
-        if (s) wi *= s[i] * s[i];
-        for (int k = 0; k < nv; ++k) acc[k] += V[k * ldv + i] * wi;
-        acc[nv] += wi * w[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += V[k * ldv + i] * wi;
+        acc[NV] += wi * wi;
     }
-    block_reduce_store<MAXV>(acc, nv + 1, partial);
+    block_reduce_store<NV + 1>(acc, partial);
 }
 
-// S^2-weighted dots split by field group: slot 2k holds the concentration part (fields 0..2) of
-// <V_k, w>_S and slot 2k+1 the potential part (field 3); slots 2nv, 2nv+1 hold <w, w>_S.
+// S^2-weighted dots split by group: slot NG*k + g holds group g's part of <V_k, w>_S and slots
+// NG*NV + g hold <w, w>_S. Groups: 0 = concentrations (fields 0..2), 1 = potentials (field 3);
+// with NG = 3, group 2 takes the extracellular potentials (elements at or past n4i).
+template <int NV, int NG>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot_split(int64_t n4, const double* __restrict__ V, int64_t ldv,
-                                                            int nv, const double* __restrict__ w,
-                                                            const double* __restrict__ s,
-                                                            double* __restrict__ partial) {
-    double acc[MAXW];
-    for (int k = 0; k < MAXW; ++k) acc[k] = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        const int grp = (i & 3) == 3;
+                                                            const double* __restrict__ w, const double* __restrict__ s,
+                                                            int64_t n4i, double* __restrict__ partial) {
+    double acc[NV + 1];
+    double out[NG * (NV + 1)];
+#pragma unroll
+    for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NG * (NV + 1); ++k) out[k] = 0.0;
+    // the grid stride is a multiple of 4, so every thread keeps the same field; a thread of the
+    // potential field crosses the region boundary at most once, which flushes its sums
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool phi = (i0 & 3) == 3;
+    int grp = phi ? ((NG == 3 && i0 >= n4i) ? 2 : 1) : 0;
+    for (int64_t i = i0; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        if (NG == 3 && phi && grp == 1 && i >= n4i) {
+#pragma unroll
+            for (int k = 0; k <= NV; ++k) {
+                out[NG * k + 1] += acc[k];
+                acc[k] = 0.0;
+            }
+            grp = 2;
+        }
         double wi = w[i] * s[i] * s[i];
-        for (int k = 0; k < nv; ++k) acc[2 * k + grp] += V[k * ldv + i] * wi;
-        acc[2 * nv + grp] += wi * w[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += V[k * ldv + i] * wi;
+        acc[NV] += wi * w[i];
     }
-    block_reduce_store<MAXW>(acc, 2 * nv + 2, partial);
+#pragma unroll
+    for (int k = 0; k <= NV; ++k) {
+        if (grp == 0) out[NG * k] += acc[k];
+        if (grp == 1) out[NG * k + 1] += acc[k];
+        if (NG == 3 && grp == 2) out[NG * k + NG - 1] += acc[k];
+    }
+    block_reduce_store<NG * (NV + 1)>(out, partial);
 }
 
 // w' = w - sum_k h[k] V_k (in place); partial sums of <V_k, w'> and <w', w'>
+template <int NV>
 __global__ void __launch_bounds__(RED_THREADS) k_orth_update_dot(int64_t n4, const double* __restrict__ V, int64_t ldv,
-                                                                 int nv, const double* __restrict__ h,
-                                                                 double* __restrict__ w, double* __restrict__ partial) {
-    double acc[MAXV];
-    for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
-    __shared__ double hs[MAXV];
-    if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
-    __syncthreads();
+                                                                 const double* __restrict__ h, double* __restrict__ w,
+                                                                 double* __restrict__ partial) {
+    double acc[NV + 1], hk[NV > 0 ? NV : 1];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) hk[k] = h[k];
+#pragma unroll
+    for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        double vk[MAXV];
+        double vk[NV > 0 ? NV : 1];
         double wi = w[i];
-        for (int k = 0; k < nv; ++k) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
             vk[k] = V[k * ldv + i];
-            wi -= hs[k] * vk[k];
+            wi -= hk[k] * vk[k];
         }
         w[i] = wi;
-        for (int k = 0; k < nv; ++k) acc[k] += vk[k] * wi;
-        acc[nv] += wi * wi;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += vk[k] * wi;
+        acc[NV] += wi * wi;
     }
-    block_reduce_store<MAXV>(acc, nv + 1, partial);
+    block_reduce_store<NV + 1>(acc, partial);
+}
+
+// v_{j+1} = (w' - sum_k h2[k] V_k) / eta with eta^2 = <w',w'> - |h2|^2 (in place). When the second
+// Gram-Schmidt pass found nothing to remove (|h2| <= ORTH_SKIP * |w'|), the subtraction is skipped,
+// V is not read, eta = |w'|, and flag[0] = 1 tells the host to keep h1 alone in the Hessenberg column.
+constexpr double ORTH_SKIP = 1e-10;
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS) k_orth_final(int64_t n4, const double* __restrict__ V, int64_t ldv,
+                                                            const double* __restrict__ h2, double* __restrict__ w,
+                                                            double* __restrict__ flag) {
+    double hk[NV > 0 ? NV : 1];
+    double hh = 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        hk[k] = h2[k];
+        hh += hk[k] * hk[k];
+    }
+    const double s2 = h2[NV];
+    const bool skip = hh <= ORTH_SKIP * ORTH_SKIP * s2;
+    const double e2 = skip ? s2 : s2 - hh;
+    const double inv_eta = e2 > 0 ? 1.0 / sqrt(e2) : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag[0] = skip ? 1.0 : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        if (!skip) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) wi -= hk[k] * V[k * ldv + i];
+        }
+        w[i] = wi * inv_eta;
+    }
 }
 
 // out[k] = sum_b partial[b][k]
@@ -122,37 +184,40 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nv
     if (threadIdx.x == 0) out[k] = sh[0];
 }
 
-// v_out = (w - sum_k h2[k] V_k) / eta, eta^2 = <w,w> - |h2|^2 (w = v_out in place)
-__global__ void k_orth_final(int64_t n4, const double* __restrict__ V, int64_t ldv, int nv,
-                             const double* __restrict__ h2, double* __restrict__ w) {
-    __shared__ double hs[MAXV];
-    __shared__ double inv_eta;
-    if (threadIdx.x < nv) hs[threadIdx.x] = h2[threadIdx.x];
-    if (threadIdx.x == 0) {
-        double s = h2[nv];
-        for (int k = 0; k < nv; ++k) s -= h2[k] * h2[k];
-        inv_eta = s > 0 ? 1.0 / sqrt(s) : 0.0;
-    }
-    __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        double wi = w[i];
-        for (int k = 0; k < nv; ++k) wi -= hs[k] * V[k * ldv + i];
-        w[i] = wi * inv_eta;
-    }
-}
-
 // x += sum_k y[k] Z_k
-__global__ void k_update_x(int64_t n4, const double* __restrict__ Z, int64_t ldz, int nz, const double* __restrict__ y,
-                           double* __restrict__ x) {
-    __shared__ double ys[MAXV];
-    if (threadIdx.x < nz) ys[threadIdx.x] = y[threadIdx.x];
-    __syncthreads();
+template <int NZ>
+__global__ void __launch_bounds__(RED_THREADS) k_update_x(int64_t n4, const double* __restrict__ Z, int64_t ldz,
+                                                          const double* __restrict__ y, double* __restrict__ x) {
+    double yk[NZ > 0 ? NZ : 1];
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) yk[k] = y[k];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         double s = x[i];
-        for (int k = 0; k < nz; ++k) s += ys[k] * Z[k * ldz + i];
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) s += yk[k] * Z[k * ldz + i];
         x[i] = s;
     }
 }
+
+#define KNP_NV_CASES(X) \
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
+    X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
+
+#define KNP_NV_CASE_k_mdot(N) case N: k_mdot<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_mdot_split2(N) case N: k_mdot_split<N, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_mdot_split3(N) case N: k_mdot_split<N, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_orth_update_dot(N) \
+    case N: k_orth_update_dot<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_orth_final(N) case N: k_orth_final<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_update_x(N) case N: k_update_x<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+// Launch KERNEL<nv><<<RED_BLOCKS, RED_THREADS, 0, st>>>(args) for a runtime nv in [0, 31]
+#define KNP_LAUNCH_NV(nv, KERNEL)                                                                    \
+    do {                                                                                             \
+        switch (nv) {                                                                                \
+            KNP_NV_CASES(KNP_NV_CASE_##KERNEL)                                                       \
+            default: KNP_FAIL(KNP_ERR_INVALID_ARG, "vector count %d out of range", (int)(nv));        \
+        }                                                                                            \
+    } while (0)
 
 __global__ void k_scale_copy(int64_t n4, const double* __restrict__ a, const double* __restrict__ s,
                              double* __restrict__ out) {
@@ -184,10 +249,10 @@ GmresWork* gmres_work(knp_problem* p, int restart) {
     g->V.alloc((restart + 1) * g->n4);
     g->Z.alloc((restart + 1) * g->n4);
     g->partial.alloc(RED_BLOCKS * MAXW);
-    g->dots.alloc(2 * MAXV + MAXW);
+    g->dots.alloc(2 * MAXV + MAXW + 1);
     g->y.alloc(MAXV);
     g->tmp.alloc(g->n4);
-    g->hh.resize(2 * MAXV + MAXW);
+    g->hh.resize(2 * MAXV + MAXW + 1);
     p->gw = g;
     return g;
 }
@@ -197,7 +262,7 @@ void gmres_free(GmresWork* g) { delete g; }
 // squared norm of a device vector (through the multi-dot kernels)
 static double norm2_dev(GmresWork& g, const double* v, cudaStream_t st) {
     count_launch(2);
-    k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(g.n4, nullptr, 0, 0, v, nullptr, g.partial.p);
+    k_mdot<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g.n4, nullptr, 0, v, g.partial.p);
     k_reduce<<<1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 1, g.dots.p);
     double s;
     KNP_CUDA(cudaMemcpyAsync(&s, g.dots.p, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -205,7 +270,8 @@ static double norm2_dev(GmresWork& g, const double* v, cudaStream_t st) {
     return s;
 }
 
-knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stats& stats) {
+knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stats& stats, double* x,
+                         const double* fvec, bool transpose) {
     auto t0 = std::chrono::steady_clock::now();
     const int m = o.restart;
     KNP_REQUIRE(m >= 1 && m + 2 <= MAXV, KNP_ERR_INVALID_ARG, "restart must be in [1, %d]", MAXV - 2);
@@ -213,30 +279,35 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     cudaStream_t st = p->stream;
     const int64_t n4 = g.n4;
     const unsigned nb = (unsigned)((n4 + 255) / 256);
-    double* x = p->u.p;
     // reference norms ||S x_0|| of the stopping test, concentrations and potentials apart
     count_launch(3);
-    k_mdot_split<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, 0, x, p->svec.p, g.partial.p);
-    k_reduce<<<2, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2, g.dots.p + 2 * MAXV);
-    double xn2[2];
-    KNP_CUDA(cudaMemcpyAsync(xn2, g.dots.p + 2 * MAXV, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    const int NG = o.phi_e_group ? 3 : 2;
+    const int64_t n4i = 4 * p->N_i;
+    if (NG == 3)
+        k_mdot_split<0, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
+    else
+        k_mdot_split<0, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
+    k_reduce<<<NG, 256, 0, st>>>(g.partial.p, RED_BLOCKS, NG, g.dots.p + 2 * MAXV);
+    double xn2[3] = {0, 0, 0};
+    KNP_CUDA(cudaMemcpyAsync(xn2, g.dots.p + 2 * MAXV, NG * sizeof(double), cudaMemcpyDeviceToHost, st));
     KNP_CUDA(cudaStreamSynchronize(st));
-    KNP_REQUIRE(std::isfinite(xn2[0]) && std::isfinite(xn2[1]), KNP_ERR_NUMERIC, "initial guess is not finite");
-    k_scale_copy<<<nb, 256, 0, st>>>(n4, p->f.p, p->sinv.p, g.tmp.p);
+    KNP_REQUIRE(std::isfinite(xn2[0]) && std::isfinite(xn2[1]) && std::isfinite(xn2[2]), KNP_ERR_NUMERIC,
+                "initial guess is not finite");
+    k_scale_copy<<<nb, 256, 0, st>>>(n4, fvec, p->sinv.p, g.tmp.p);
     count_launch();
     const double bnorm = std::sqrt(norm2_dev(g, g.tmp.p, st));
     KNP_REQUIRE(std::isfinite(bnorm), KNP_ERR_NUMERIC, "right-hand side is not finite");
     knp_status_detail res{KNP_OK, 0, 0, 0.0};
-    double tol[2];
-    for (int q = 0; q < 2; ++q) tol[q] = o.rtol * (xn2[q] > 0 ? std::sqrt(xn2[q]) : 1.0);
+    double tol[3];
+    for (int q = 0; q < NG; ++q) tol[q] = o.rtol * std::sqrt(std::max(xn2[q], 0.0));
     const int m1 = m + 1;
-    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), G(2 * m1 * m1);
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), G(NG * m1 * m1);
     int its = 0, restarts = 0;
     bool converged = false;
     double beta = 0;
     while (!converged) {
         // V_0 = S^-1 (f - A x)
-        op_apply(p, x, g.V.p, p->sinv.p, p->f.p);
+        op_apply(p, x, g.V.p, p->sinv.p, fvec, transpose);
         beta = std::sqrt(norm2_dev(g, g.V.p, st));
         KNP_REQUIRE(std::isfinite(beta), KNP_ERR_NUMERIC, "residual is not finite");
         if (beta == 0.0) {
@@ -256,28 +327,40 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
             // z_j = V-cycle(S v_j); row j of the S^2-weighted Gram matrices of Z (two field groups)
             vcycle_apply(p, vj, p->svec.p, zj);
             count_launch(2);
-            k_mdot_split<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.Z.p, n4, j, zj, p->svec.p, g.partial.p);
-            k_reduce<<<2 * j + 2, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2 * j + 2, g.dots.p + 2 * MAXV);
+#define KNP_ARGS n4, g.Z.p, n4, zj, p->swt.p, n4i, g.partial.p
+            if (NG == 3)
+                KNP_LAUNCH_NV(j, k_mdot_split3);
+            else
+                KNP_LAUNCH_NV(j, k_mdot_split2);
+#undef KNP_ARGS
+            k_reduce<<<NG * (j + 1), 256, 0, st>>>(g.partial.p, RED_BLOCKS, NG * (j + 1), g.dots.p + 2 * MAXV);
             const bool arnoldi = (j < m) && (its < o.max_it);
             int nv = j + 1;
             if (arnoldi) {
                 double* w = g.V.p + (int64_t)(j + 1) * n4;
-                op_apply(p, zj, w, p->sinv.p, nullptr);
+                op_apply(p, zj, w, p->sinv.p, nullptr, transpose);
                 ProfScope ps(&p->prof, KC_ORTHO, st);
                 count_launch(5);
-                k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, w, nullptr, g.partial.p);
+#define KNP_ARGS n4, g.V.p, n4, w, g.partial.p
+                KNP_LAUNCH_NV(nv, k_mdot);
+#undef KNP_ARGS
                 k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p);
-                k_orth_update_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, g.dots.p, w, g.partial.p);
+#define KNP_ARGS n4, g.V.p, n4, g.dots.p, w, g.partial.p
+                KNP_LAUNCH_NV(nv, k_orth_update_dot);
+#undef KNP_ARGS
                 k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p + MAXV);
-                k_orth_final<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.V.p, n4, nv, g.dots.p + MAXV, w);
+#define KNP_ARGS n4, g.V.p, n4, g.dots.p + MAXV, w, g.dots.p + 2 * MAXV + MAXW
+                KNP_LAUNCH_NV(nv, k_orth_final);
+#undef KNP_ARGS
             }
-            KNP_CUDA(cudaMemcpyAsync(g.hh.data(), g.dots.p, (2 * MAXV + MAXW) * sizeof(double),
+            KNP_CUDA(cudaMemcpyAsync(g.hh.data(), g.dots.p, (2 * MAXV + MAXW + 1) * sizeof(double),
                                      cudaMemcpyDeviceToHost, st));
             KNP_CUDA(cudaStreamSynchronize(st));
             KNP_CUDA(cudaGetLastError());
-            for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < NG; ++q)
                 for (int a = 0; a <= j; ++a)
-                    G[q * m1 * m1 + j * m1 + a] = G[q * m1 * m1 + a * m1 + j] = g.hh[2 * MAXV + 2 * a + q];
+                    G[q * m1 * m1 + j * m1 + a] = G[q * m1 * m1 + a * m1 + j] = g.hh[2 * MAXV + NG * a + q];
+
             // preconditioned residual of the iterate after k_done = j steps: M^-1 r = Z c with
             // c = Q^T (0, .., 0, g_j); its S-norm is sqrt(c^T G c)
             {
@@ -289,13 +372,23 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                     c[i] = cs[i] * a - sn[i] * b;
                     c[i + 1] = sn[i] * a + cs[i] * b;
                 }
+                // the correction of this cycle, x_k - x_0 = Z y_k, and its S-norms y^T G y
+                std::vector<double> yk(k);
+                for (int i = k - 1; i >= 0; --i) {
+                    double sacc = gv[i];
+                    for (int q2 = i + 1; q2 < k; ++q2) sacc -= H[i * m + q2] * yk[q2];
+                    yk[i] = sacc / H[i * m + i];
+                }
                 bool ok = true;
-                for (int q = 0; q < 2; ++q) {
-                    double est2 = 0;
+                for (int q = 0; q < NG; ++q) {
+                    double est2 = 0, corr2 = 0;
                     for (int a = 0; a <= k; ++a)
                         for (int b = 0; b <= k; ++b) est2 += c[a] * c[b] * G[q * m1 * m1 + a * m1 + b];
+                    for (int a = 0; a < k; ++a)
+                        for (int b = 0; b < k; ++b) corr2 += yk[a] * yk[b] * G[q * m1 * m1 + a * m1 + b];
                     KNP_REQUIRE(std::isfinite(est2), KNP_ERR_NUMERIC, "preconditioned residual is not finite");
-                    ok &= std::sqrt(std::max(est2, 0.0)) <= tol[q];
+                    const double ref = std::max(tol[q], o.rtol * std::sqrt(std::max(corr2, 0.0)));
+                    ok &= std::sqrt(std::max(est2, 0.0)) <= ref;
                 }
                 if (ok) {
                     converged = true;
@@ -307,11 +400,13 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                 k_done = j;
                 break;
             }
+            // second pass skipped on the device (flag): the column is h1 and eta = |w'|
+            const bool skipped = g.hh[2 * MAXV + MAXW] != 0.0;
             double s2 = g.hh[MAXV + nv];
             double eta2 = s2;
             for (int k = 0; k < nv; ++k) {
-                H[k * m + j] = g.hh[k] + g.hh[MAXV + k];
-                eta2 -= g.hh[MAXV + k] * g.hh[MAXV + k];
+                H[k * m + j] = g.hh[k] + (skipped ? 0.0 : g.hh[MAXV + k]);
+                if (!skipped) eta2 -= g.hh[MAXV + k] * g.hh[MAXV + k];
             }
             KNP_REQUIRE(std::isfinite(eta2), KNP_ERR_NUMERIC, "Arnoldi vector is not finite");
             double eta = eta2 > 0 ? std::sqrt(eta2) : 0.0;
@@ -345,7 +440,9 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
             }
             KNP_CUDA(cudaMemcpyAsync(g.y.p, y.data(), k_done * sizeof(double), cudaMemcpyHostToDevice, st));
             count_launch();
-            k_update_x<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, g.Z.p, n4, k_done, g.y.p, x);
+#define KNP_ARGS n4, g.Z.p, n4, g.y.p, x
+            KNP_LAUNCH_NV(k_done, k_update_x);
+#undef KNP_ARGS
             KNP_CUDA(cudaGetLastError());
         }
         if (!converged && its >= o.max_it) {
@@ -354,7 +451,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         }
     }
     // report the scaled true residual of the final iterate
-    op_apply(p, x, g.tmp.p, p->sinv.p, p->f.p);
+    op_apply(p, x, g.tmp.p, p->sinv.p, fvec, transpose);
     double rn = std::sqrt(norm2_dev(g, g.tmp.p, st));
     double relres = bnorm > 0 ? rn / bnorm : 0.0;
     if (!converged) res.code = KNP_ERR_NOT_CONVERGED;

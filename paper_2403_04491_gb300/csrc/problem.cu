@@ -369,6 +369,19 @@ void build_problem(knp_problem* P) {
         }
     }
     KNP_REQUIRE(S.n_entries < INT32_MAX, KNP_ERR_INVALID_ARG, "pattern too large for 32-bit positions");
+    // transposed cross-region list (used by the transposed operator)
+    std::vector<int32_t> xtp(n + 1, 0), xtr(xc.size()), xti(xc.size());
+    for (size_t t = 0; t < xc.size(); ++t) xtp[xc[t] + 1]++;
+    for (int64_t r = 0; r < n; ++r) xtp[r + 1] += xtp[r];
+    {
+        std::vector<int32_t> fill(xtp.begin(), xtp.end() - 1);
+        for (int64_t r = 0; r < n; ++r)
+            for (int32_t t = xp[r]; t < xp[r + 1]; ++t) {
+                int32_t q = fill[xc[t]]++;
+                xtr[q] = (int32_t)r;
+                xti[q] = t;
+            }
+    }
 
     // ---- uploads
     S.slice_ptr.upload(S.h_slice_ptr, st);
@@ -380,6 +393,9 @@ void build_problem(knp_problem* P) {
     P->sell_e.zero(st);
     P->xptr.upload(xp, st);
     P->xcol.upload(xc, st);
+    P->xtptr.upload(xtp, st);
+    P->xtrow.upload(xtr, st);
+    P->xtidx.upload(xti, st);
     P->xe.alloc(std::max<int64_t>(1, 3 * (int64_t)xc.size()));
     P->xe.zero(st);
     P->el_nodes.upload(eln, st);
@@ -407,6 +423,7 @@ void build_problem(knp_problem* P) {
     P->f.zero(st);
     P->sinv.alloc(4 * n);
     P->svec.alloc(4 * n);
+    P->swt.alloc(4 * n);
     const knp_problem_desc& d = P->desc;
     count_launch(nmv ? 2 : 1);
     k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
@@ -414,6 +431,41 @@ void build_problem(knp_problem* P) {
     if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
     KNP_CUDA(cudaGetLastError());
     KNP_CUDA(cudaStreamSynchronize(st));
+}
+
+// Element stiffness matrices [n_elem][4][4] (elements in el_nodes order) and the node -> element
+// incidence, for the adjoint of the weighted stiffness A_r^{k}(c).
+void build_problem_stiffness(knp_problem* P, std::vector<double>& elA, std::vector<int32_t>& neptr,
+                             std::vector<int32_t>& nelist) {
+    const knp_mesh& m = *P->mesh;
+    const int dim = m.dim, nvpe = dim + 1;
+    const int64_t n = P->n_nodes;
+    std::vector<int32_t> src;
+    src.insert(src.end(), m.elems_i.begin(), m.elems_i.end());
+    src.insert(src.end(), m.elems_e.begin(), m.elems_e.end());
+    elA.assign(src.size() * 16, 0.0);
+    neptr.assign(n + 1, 0);
+    std::vector<int32_t> gl(src.size() * nvpe);
+    for (size_t e = 0; e < src.size(); ++e) {
+        double vol, G[4][3];
+        simplex_geometry(m.coords.data(), dim, &m.elems[(int64_t)src[e] * nvpe], vol, G);
+        for (int j = 0; j < nvpe; ++j) {
+            for (int l = 0; l < nvpe; ++l) {
+                double s = 0;
+                for (int d = 0; d < dim; ++d) s += G[j][d] * G[l][d];
+                elA[e * 16 + j * 4 + l] = vol * s;
+            }
+            int32_t v = m.elems[(int64_t)src[e] * nvpe + j];
+            int32_t g = e < m.elems_i.size() ? m.loc_i[v] : (int32_t)(P->N_i + m.loc_e[v]);
+            gl[e * nvpe + j] = g;
+            neptr[g + 1]++;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) neptr[i + 1] += neptr[i];
+    nelist.assign(neptr[n], 0);
+    std::vector<int32_t> fill(neptr.begin(), neptr.end() - 1);
+    for (size_t e = 0; e < src.size(); ++e)
+        for (int j = 0; j < nvpe; ++j) nelist[fill[gl[e * nvpe + j]]++] = (int32_t)e;
 }
 
 void download_state(const knp_problem* p, std::vector<double>& u) {

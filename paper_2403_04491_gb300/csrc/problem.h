@@ -85,6 +85,7 @@ struct StepParams {
 
 struct AmgHierarchy;        // vcycle.cu
 struct GmresWork;           // gmres.cu
+struct AdjointWork;         // adjoint.cu
 
 }  // namespace knp
 
@@ -111,6 +112,7 @@ struct knp_problem {
     std::vector<int32_t> h_xptr, h_xcol;
     knp::DArray<int32_t> xptr, xcol;     // cross-region entries, CSR over rows
     knp::DArray<double> xe;              // [3][n_cross]
+    knp::DArray<int32_t> xtptr, xtrow, xtidx;   // the cross entries by column: (row, value index)
 
     // bulk assembly data
     knp::DArray<int32_t> el_nodes;       // [n_elem][dim+1] global node ids
@@ -138,18 +140,28 @@ struct knp_problem {
     knp::DArray<double> f;               // right-hand side f_n
     knp::DArray<double> sinv;            // 1/sqrt(diag P_0) (set by knp_amg_setup)
     knp::DArray<double> svec;            // sqrt(diag P_0)
+    knp::DArray<double> swt;             // weights of the stopping test: svec, 0 on the pinned phi_e
 
     knp::Profiler prof;
     knp::AmgHierarchy* amg = nullptr;
     knp::GmresWork* gw = nullptr;
+    knp::AdjointWork* adj = nullptr;
     ~knp_problem();
 };
 
 namespace knp {
 // assemble.cu
 void launch_assembly(knp_problem* p);
+double stimulus_at(const knp_problem_desc& d, double t);
+// adjoint.cu
+void adjoint_free(AdjointWork* w);
+void adjoint_begin(knp_problem* P);
+void adjoint_step(knp_problem* P, bool device, const double* u_n, const double* dLdu, const knp_solve_opts& o,
+                  knp_solve_stats& stats);
+void adjoint_get(knp_problem* P, bool device, double* dLdu0, double* dLdw0, double* grad, double* lambda);
 // spmv.cu
 // y = A x (unscaled), or with row scaling / residual; see spmv.cu
-void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b);
+void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b,
+              bool transpose = false);
 void download_state(const knp_problem* p, std::vector<double>& u);
 }  // namespace knp

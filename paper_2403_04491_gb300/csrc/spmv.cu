@@ -9,6 +9,10 @@
 // (B_rq) carry -[C_r^k M_{rq,Gamma}] in the same e^k slot with m = a = 0. Per entry the
 // kernel needs nine FMAs (sum m x^k, sum a x^k, sum e^k phi) instead of sixteen.
 // One thread per row; the sliced-ELL layout makes the value loads of a warp contiguous.
+//
+// Point pin (Remark 4.1): the stored values keep the phi_e column of the pinned node (so the
+// same-region values stay symmetric and serve the transpose too); both kernels treat that
+// column as zero and give the pinned phi_e row the identity.
 #include "problem.h"
 
 namespace knp {
@@ -27,6 +31,9 @@ struct OpArgs {
     const int32_t* xcol;
     const double* xe;
     int64_t n_cross;
+    const int32_t* xtptr;   // transposed cross-region entries: row -> (source row, value index)
+    const int32_t* xtrow;
+    const int32_t* xtidx;
     double tau[2][KI];
     double z[KI];
 };
@@ -47,18 +54,20 @@ __global__ void __launch_bounds__(128) k_op_apply(OpArgs A, const double* __rest
         const double2* xp = reinterpret_cast<const double2*>(x + 4 * c);
         double2 x01 = xp[0], x23 = xp[1];
         double mv = A.m[pos], av = A.a[pos];
+        double phi = (c == A.pin) ? 0.0 : x23.y;
         am[0] += mv * x01.x;
         am[1] += mv * x01.y;
         am[2] += mv * x23.x;
         aa[0] += av * x01.x;
         aa[1] += av * x01.y;
         aa[2] += av * x23.x;
-        ae[0] += A.e[pos] * x23.y;
-        ae[1] += A.e[A.n_entries + pos] * x23.y;
-        ae[2] += A.e[2 * A.n_entries + pos] * x23.y;
+        ae[0] += A.e[pos] * phi;
+        ae[1] += A.e[A.n_entries + pos] * phi;
+        ae[2] += A.e[2 * A.n_entries + pos] * phi;
     }
     for (int t = A.xptr[r]; t < A.xptr[r + 1]; ++t) {
-        double phi = x[4 * (int64_t)A.xcol[t] + 3];
+        int64_t c = A.xcol[t];
+        double phi = (c == A.pin) ? 0.0 : x[4 * c + 3];
         for (int k = 0; k < KI; ++k) ae[k] += A.xe[k * A.n_cross + t] * phi;
     }
     double out[4];
@@ -80,9 +89,58 @@ __global__ void __launch_bounds__(128) k_op_apply(OpArgs A, const double* __rest
     yp[1] = make_double2(out[2], out[3]);
 }
 
+// y = rowscale .* (b - A^T x): the transposed node block of entry (j, l) is
+//     c^k row:  (m + tau^k a) x^k_j + z_k tau^k a x^phi_j,   phi row:  sum_k e^k (x^k_j + z_k x^phi_j)
+// with m, a, e symmetric on same-region entries; the cross-region part uses the transposed list.
+__global__ void __launch_bounds__(128) k_op_apply_t(OpArgs A, const double* __restrict__ x, double* __restrict__ y,
+                                                    const double* __restrict__ rowscale,
+                                                    const double* __restrict__ b) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= A.n) return;
+    const int reg = r < A.N_i ? 0 : 1;
+    int64_t s = r / SELL_C;
+    int64_t base = A.slice_ptr[s] + r % SELL_C;
+    int64_t w = (A.slice_ptr[s + 1] - A.slice_ptr[s]) / SELL_C;
+    double am[KI] = {0, 0, 0}, aa[KI] = {0, 0, 0}, ap = 0.0, ae = 0.0;
+    for (int64_t k = 0; k < w; ++k) {
+        int64_t pos = base + k * SELL_C;
+        int64_t c = A.col[pos];
+        const double2* xp = reinterpret_cast<const double2*>(x + 4 * c);
+        double2 x01 = xp[0], x23 = xp[1];
+        double xc[KI] = {x01.x, x01.y, x23.x};
+        double phi = (c == A.pin) ? 0.0 : x23.y;
+        double mv = A.m[pos], av = A.a[pos];
+        for (int q = 0; q < KI; ++q) {
+            am[q] += mv * xc[q];
+            aa[q] += av * xc[q];
+            ae += A.e[q * A.n_entries + pos] * (xc[q] + A.z[q] * phi);
+        }
+        ap += av * phi;
+    }
+    for (int t = A.xtptr[r]; t < A.xtptr[r + 1]; ++t) {
+        int64_t j = A.xtrow[t];
+        int64_t idx = A.xtidx[t];
+        double phi = (j == A.pin) ? 0.0 : x[4 * j + 3];
+        for (int q = 0; q < KI; ++q) ae += A.xe[q * A.n_cross + idx] * (x[4 * j + q] + A.z[q] * phi);
+    }
+    double out[4];
+    for (int q = 0; q < KI; ++q) out[q] = am[q] + A.tau[reg][q] * (aa[q] + A.z[q] * ap);
+    out[3] = ae;
+    if (r == A.pin) out[3] = x[4 * r + 3];
+    if (b) {
+        for (int q = 0; q < 4; ++q) out[q] = b[4 * r + q] - out[q];
+    }
+    if (rowscale) {
+        for (int q = 0; q < 4; ++q) out[q] *= rowscale[4 * r + q];
+    }
+    double2* yp = reinterpret_cast<double2*>(y + 4 * r);
+    yp[0] = make_double2(out[0], out[1]);
+    yp[1] = make_double2(out[2], out[3]);
+}
+
 }  // namespace
 
-void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b) {
+void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b, bool transpose) {
     OpArgs A;
     A.n = p->n_nodes;
     A.N_i = p->N_i;
@@ -97,13 +155,19 @@ void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale
     A.xcol = p->xcol.p;
     A.xe = p->xe.p;
     A.n_cross = (int64_t)p->h_xcol.size();
+    A.xtptr = p->xtptr.p;
+    A.xtrow = p->xtrow.p;
+    A.xtidx = p->xtidx.p;
     for (int r = 0; r < 2; ++r)
         for (int k = 0; k < KI; ++k) A.tau[r][k] = p->sp.reg[r].tau[k];
     for (int k = 0; k < KI; ++k) A.z[k] = p->sp.z[k];
     unsigned blocks = (unsigned)((A.n + 127) / 128);
     ProfScope ps(&p->prof, KC_SPMV, p->stream);
     count_launch();
-    k_op_apply<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
+    if (transpose)
+        k_op_apply_t<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
+    else
+        k_op_apply<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
     KNP_CUDA(cudaGetLastError());
 }
 

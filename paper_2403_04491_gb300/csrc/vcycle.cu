@@ -229,9 +229,11 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
-int pick_tpr(double mean_len) {
+// threads per row, a power of two in [1, 32]: enough groups to fill the GPU (about 2 x 152 SMs
+// x 1024 threads) on small coarse levels, and at least two entries per lane
+int pick_tpr(int64_t rows, double mean_len) {
     int t = 1;
-    while (t < 32 && t * 2 <= mean_len) t *= 2;
+    while (t < 32 && (double)rows * t < 311296.0 && t * 4 <= mean_len) t *= 2;
     return t;
 }
 
@@ -246,7 +248,7 @@ struct DevCsr4 {
     DArray<T> val;
     void upload(const HostCsr4& h, cudaStream_t st) {
         n = h.n_rows;
-        tpr = pick_tpr(n ? (double)h.nnz() / (double)n : 1.0);
+        tpr = pick_tpr(n, n ? (double)h.nnz() / (double)n : 1.0);
         ptr.upload(h.ptr, st);
         col.upload(h.col, st);
         val.upload(cast_vec<T>(h.val), st);

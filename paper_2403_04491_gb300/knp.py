@@ -62,7 +62,7 @@ class AmgOpts(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32)]
+    _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32), ("phi_e_group", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -104,6 +104,11 @@ SIGNATURES = {
     "knp_apply_preconditioner_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p],
     "knp_amg_info": [C.c_void_p, _IP, _LP, _LP, _DP],
     "knp_problem_get_info": [C.c_void_p, C.c_void_p],
+    "knp_problem_set_facet_gleak": [C.c_void_p, C.c_int32, C.c_void_p],
+    "knp_adjoint_begin": [C.c_void_p],
+    "knp_adjoint_step": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveStats)],
+    "knp_adjoint_get": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "knp_apply_operator_transpose": [C.c_void_p, _DP, _DP],
     "knp_profile_begin": [C.c_void_p, C.c_int32],
     "knp_profile_end": [C.c_void_p, _LP, _DP],
     "knp_launch_count": [_LP],
@@ -260,14 +265,14 @@ class Problem:
         o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop)
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
-    def solve(self, rtol=1e-10, restart=30, max_it=1000):
-        o = SolveOpts(rtol, restart, max_it)
+    def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
         s = SolveStats()
         _check(_lib.knp_solve(self.handle, C.byref(o), C.byref(s)))
         return {"iterations": s.iterations, "restarts": s.restarts, "true_relres": s.true_relres, "ms": s.ms}
 
-    def step(self, nsteps=1, rtol=1e-10, restart=30, max_it=1000):
-        o = SolveOpts(rtol, restart, max_it)
+    def step(self, nsteps=1, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
         st = (StepStats * max(nsteps, 1))()
         _check(_lib.knp_step(self.handle, nsteps, C.byref(o), st))
         return [{"iterations": st[i].iterations, "true_relres": st[i].true_relres} for i in range(nsteps)]
@@ -308,6 +313,48 @@ class Problem:
         y = np.empty(self.n_dof)
         _check(_lib.knp_apply_operator(self.handle, _dptr(x), _dptr(y)))
         return y
+
+    def apply_operator_transpose(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(self.n_dof)
+        _check(_lib.knp_apply_operator_transpose(self.handle, _dptr(x), _dptr(y)))
+        return y
+
+    def set_facet_gleak(self, gleak):
+        """knp_problem_set_facet_gleak from a numpy array or a CUDA tensor [n_facets, n_ions]."""
+        if hasattr(gleak, "data_ptr") and getattr(gleak, "is_cuda", False):
+            _check(_lib.knp_problem_set_facet_gleak(self.handle, KNP_DEVICE, C.c_void_p(gleak.data_ptr())))
+        else:
+            g = np.ascontiguousarray(gleak, dtype=np.float64)
+            _check(_lib.knp_problem_set_facet_gleak(self.handle, KNP_HOST, g.ctypes.data_as(C.c_void_p)))
+
+    # -- adjoint
+    def adjoint_begin(self):
+        _check(_lib.knp_adjoint_begin(self.handle))
+
+    def adjoint_step(self, u_n, dLdu_n, rtol=1e-10, restart=30, max_it=1000, phi_e_group=True):
+        """u_n, dLdu_n in the Eq. 4.2 order: numpy arrays (host) or CUDA tensors (device)."""
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
+        s = SolveStats()
+        if hasattr(u_n, "data_ptr"):
+            _check(_lib.knp_adjoint_step(self.handle, KNP_DEVICE, C.c_void_p(u_n.data_ptr()),
+                                         C.c_void_p(dLdu_n.data_ptr()), C.byref(o), C.byref(s)))
+        else:
+            a = np.ascontiguousarray(u_n, dtype=np.float64)
+            b = np.ascontiguousarray(dLdu_n, dtype=np.float64)
+            _check(_lib.knp_adjoint_step(self.handle, KNP_HOST, a.ctypes.data_as(C.c_void_p),
+                                         b.ctypes.data_as(C.c_void_p), C.byref(o), C.byref(s)))
+        return {"iterations": s.iterations, "true_relres": s.true_relres}
+
+    def adjoint_get(self):
+        du = np.empty(self.n_dof)
+        dw = np.empty((3, max(self.n_mv, 1)))
+        nf = self.mesh.info["n_facets"]
+        gg = np.empty((max(nf, 1), self.n_ions))
+        lam = np.empty(self.n_dof)
+        _check(_lib.knp_adjoint_get(self.handle, KNP_HOST, du.ctypes.data_as(C.c_void_p), dw.ctypes.data_as(C.c_void_p),
+                                    gg.ctypes.data_as(C.c_void_p), lam.ctypes.data_as(C.c_void_p)))
+        return {"dLdu0": du, "dLdw0": dw[:, :self.n_mv], "grad_gleak": gg[:nf], "lambda": lam}
 
     def operator_entries(self, rows, cols):
         rows = np.ascontiguousarray(rows, dtype=np.int64)

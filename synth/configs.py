@@ -126,3 +126,18 @@ def model_a(dim: int, nx: int, dt: float) -> Config:
 
 
 CONFIGS = {i: (lambda i=i: make_config(i)) for i in range(1, 6)}
+
+
+def probe_points(cfg: Config, n: int = 64, seed: int = 2) -> np.ndarray:
+    """n points uniform in the extracellular space (rejection against the snapped cell boxes),
+    strictly inside the domain; PCG64(seed)."""
+    m = cfg.mesh
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = []
+    while len(pts) < n:
+        p = rng.uniform(0.02, 0.98, size=cfg.dim)
+        g = p * cfg.nx
+        inside = np.any(np.all((g >= m.boxes[:, 0] - 1e-9) & (g <= m.boxes[:, 1] + 1e-9), axis=1))
+        if not inside:
+            pts.append(p * cfg.length)
+    return np.array(pts)

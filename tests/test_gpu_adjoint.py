@@ -1,0 +1,115 @@
+"""GPU adjoint against the oracle's adjoint (autograd of its torch residual form, exact LU
+solves): the transposed operator, and the gradients of L = sum_n sum_p phi_e(x_p, t_n)^2 with
+respect to the per-facet K leak conductance, u_0 and the HH gates w_0; and the
+torch.autograd.Function with checkpointing.
+
+Given the oracle's forward states, the GPU reverse sweep matches to relative l2 1e-6. From the
+GPU's own forward run the bar is 1e-5: the loss is built from phi_e, about 1e-8 of phi_i here,
+and the block-diagonal preconditioner's error estimate (the stopping test) sees phi_e's error
+only through its own block, so FGMRES at rtol 1e-12 leaves phi_e with relative errors near 1e-6.
+"""
+import numpy as np
+import pytest
+
+from helpers import blockwise_vector_error
+from oracle import adjoint as oadj, problem as oproblem, system as osystem
+from synth import make_config
+from synth.configs import probe_points
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+CASES = {"cfg4-16cells-32": (make_config(4).with_nx(32), 4), "cfg2-hh-8": (make_config(2).with_nx(8), 3)}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_transposed_operator(name):
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg, _ = CASES[name]
+    pb, s0 = oproblem.from_config(cfg)
+    A, f, _ = osystem.assemble(pb, s0)
+    _, prob = problem_from_config(cfg)
+    prob.assemble_step()
+    x = np.random.default_rng(5).standard_normal(A.shape[0])
+    assert blockwise_vector_error(pb, prob.apply_operator_transpose(x), A.T @ x) < 1e-12
+
+
+def _gpu_sweep(cfg, n_steps, Pmat, oracle_states=None):
+    """Reverse sweep on the GPU, from its own forward run (rtol 1e-12, extracellular potentials
+    tested as their own group) or from given states."""
+    from paper_2403_04491_gb300 import problem_from_config
+    _, prob = problem_from_config(cfg)
+    prob.amg_setup()
+    pack = lambda s: np.concatenate([s["c_i"].ravel(), s["phi_i"], s["c_e"].ravel(), s["phi_e"]])
+    if oracle_states is None:
+        states = [prob.state_get()]
+        for _ in range(n_steps):
+            prob.step(1, rtol=1e-12, phi_e_group=True)
+            states.append(prob.state_get())
+    else:
+        states = [dict(c_i=s.c_i, phi_i=s.phi_i, c_e=s.c_e, phi_e=s.phi_e, w=s.w, t=s.t) for s in oracle_states]
+    prob.adjoint_begin()
+    for n in range(n_steps, 0, -1):
+        u_n = pack(states[n])
+        dLdu = 2.0 * (Pmat.T @ (Pmat @ u_n))
+        s = states[n - 1]
+        prob.state_set(s["c_i"], s["phi_i"], s["c_e"], s["phi_e"], s["w"], s["t"])
+        prob.adjoint_step(u_n, dLdu, rtol=1e-12)
+    return prob.adjoint_get(), prob
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("own_forward", [False, True], ids=["oracle-states", "gpu-forward"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_gradients_match_oracle_adjoint(name, own_forward):
+    cfg, n_steps = CASES[name]
+    pb, s0 = oproblem.from_config(cfg)
+    Pmat = oadj.probe_matrix(pb, probe_points(cfg))
+    ref = oadj.run_with_adjoint(pb, s0, n_steps, Pmat)
+    got, prob = _gpu_sweep(cfg, n_steps, Pmat, None if own_forward else ref["states"])
+    Ni = pb.topo.N_i
+    tol = 1e-5 if own_forward else 1e-6
+    assert _rel(got["grad_gleak"], ref["grad_gleak"]) < tol
+    assert _rel(got["dLdu0"][Ni:2 * Ni], ref["dLdu0"][Ni:2 * Ni]) < tol      # initial [K]_i
+    mask = np.ones(len(ref["dLdu0"]), bool)
+    mask[osystem.pin_dof(pb)] = False                                        # the pinned unknown is not a variable
+    assert _rel(got["dLdu0"][mask], ref["dLdu0"][mask]) < tol
+    if np.linalg.norm(ref["dLdw0"]) > 0:
+        assert _rel(got["dLdw0"], ref["dLdw0"]) < tol
+
+
+def test_autograd_function_with_checkpoints():
+    import torch
+    from paper_2403_04491_gb300 import KNPFunction, Simulation, problem_from_config, probe_weights
+    cfg = make_config(4).with_nx(32)
+    n_steps = 5
+    mesh, prob = problem_from_config(cfg)
+    prob.amg_setup()
+    m = cfg.mesh
+    ni, ne = mesh.nodes()
+    idx, w = probe_weights(m.coords, m.elems, m.elem_tag, ne, prob.N_i, prob.N_e, probe_points(cfg))
+    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=2, rtol=1e-12)
+    gK = torch.tensor(prob._facet_gleak[:, 1].copy(), requires_grad=True)
+    cK = torch.tensor(sim.s0["c_i"][1].copy(), requires_grad=True)
+    traces = KNPFunction.apply(gK, cK, sim)
+    loss = (traces ** 2).sum()
+    loss.backward()
+    pb, s0 = oproblem.from_config(cfg)
+    Pmat = oadj.probe_matrix(pb, probe_points(cfg))
+    ref = oadj.run_with_adjoint(pb, s0, n_steps, Pmat)
+    assert abs(float(loss) - ref["L"]) < 1e-6 * ref["L"]
+    Ni = pb.topo.N_i
+    assert _rel(gK.grad.numpy(), ref["grad_gleak"][:, 1]) < 1e-5
+    assert _rel(cK.grad.numpy(), ref["dLdu0"][Ni:2 * Ni]) < 1e-5
