@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -241,6 +242,14 @@ def ours(args):
 
     # end to end through the public API with host buffers: per step the state goes host->device,
     # one knp_step runs, and the new state comes back device->host (pinned host memory)
+    e2e = None if args.no_e2e else e2e_run(prob, torch, args, n_dof, world)
+    mixed = None if args.no_mixed else mixed_run(cfg, mesh, torch, args, n_dof)
+    report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg)
+
+
+def e2e_run(prob, torch, args, n_dof, world):
+    import numpy as np
+    import torch.distributed as dist
     st = prob.state_get()
     host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in ("c_i", "phi_i", "c_e", "phi_e", "w")}
     dev = {k: torch.empty(v.shape, dtype=torch.float64, device="cuda") for k, v in host.items()}
@@ -272,10 +281,15 @@ def ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = n_dof * args.steps * world / (e2e_ms / 1e3)
+    return dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=h2d)
 
-    # mixed-precision form (FP32 hierarchy and V-cycle under FP64 FGMRES), same workload
+
+def mixed_run(cfg, mesh, torch, args, n_dof):
+    """The mixed-precision form (FP32 hierarchy and V-cycle under FP64 FGMRES), same workload."""
+    import numpy as np
+    from paper_2403_04491_gb300 import problem_from_config
     mixed = None
-    if not args.no_mixed and args.precision == "fp64":
+    if args.precision == "fp64":
         out = {}
         for rt in (1e-10, 1e-8):
             _, pm = problem_from_config(cfg, mesh=mesh)
@@ -294,8 +308,16 @@ def ours(args):
         out["fp64_rtol_1e-08"] = dict(value=n_dof * args.steps / (msf / 1e3), iters_per_step=float(np.mean(itf)))
         out["speedup_fp32_vs_fp64_at_rtol_1e-08"] = out["rtol_1e-08"]["value"] / out["fp64_rtol_1e-08"]["value"]
         mixed = out
+    return mixed
 
+
+def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg):
+    import numpy as np
+    import torch.distributed as dist
+    value = n_dof * args.steps * world / (ms / 1e3)
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -329,8 +351,7 @@ def ours(args):
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 iters_per_step=float(np.mean(iters)), iters=iters, setup_s=dict(create=t_create, amg=t_amg),
                 amg=prob.amg_info(), gpu_launches=launches, clocks=clocks, roofline=roof,
-                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=h2d),
-                cpu_baseline=cpu, mixed=mixed)
+                e2e=e2e, cpu_baseline=cpu, mixed=mixed)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
