@@ -159,20 +159,44 @@ class ClockSampler:
 # --------------------------------------------------------------------------- our arm
 
 def kernel_source_hash():
-    h = hashlib.sha256()
-    for f in ("vcycle.cu", "problem.h", "amg_setup.cpp"):
-        h.update(open(os.path.join(ROOT, "paper_2403_04491_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
+    """Hash of the source text of the finest-level Chebyshev step (sell_row, cheb_update,
+    k_cheb_sell), so that DRAM counters taken on an older version of it are not reported."""
+    src = open(os.path.join(ROOT, "paper_2403_04491_gb300", "csrc", "vcycle.cu")).read()
+    parts = []
+    for start, end in (("// Row product of a sliced-ELL operator", "// Row product of a CSR operator"),
+                       ("// Chebyshev update of one row", "template <class T, int TPR>\n__global__ void __launch_bounds__(128) k_cheb_csr")):
+        i = src.index(start)
+        parts.append(src[i:src.index(end, i)])
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
-def dominant_kernel_bytes(prob, precision):
-    """Algorithmic bytes of one finest-level Chebyshev step: the operator once (column index +
-    four values per stored entry) and six node vectors (x gathered, x itself, b, D^-1, d in/out
-    counted as the update reads d and writes d and x_out) of four values each."""
+def fp64_peak_tflops(torch):
+    """Measured FP64 rate of this GPU: best of five 4096^3 DGEMMs (cuBLAS)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def dominant_kernel_work(prob, precision):
+    """Algorithmic bytes and FLOPs of one finest-level Chebyshev step. Bytes: the operator once
+    (column index + four values per stored entry) and six node vectors of four values (x gathered,
+    b, D^-1, d read, d written, x written). FLOPs: 4 FMAs per stored entry and 20 per row."""
     info = prob.amg_info()
     n, nnz = info["nodes"][0], info["nnz"][0]
     t = 8 if precision == "fp64" else 4
-    return nnz * (4 + 4 * t) + n * 4 * t * 6
+    return nnz * (4 + 4 * t) + n * 4 * t * 6, 8.0 * nnz + 20.0 * n
 
 
 def measure(prob, torch, steps, rtol, kernel_class=None):
@@ -323,20 +347,32 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     n_launch, prof_ms = prof
-    bytes_per = dominant_kernel_bytes(prob, args.precision)
-    achieved = bytes_per / (prof_ms / n_launch / 1e3) / 1e9 if n_launch else None
+    bytes_per, flops_per = dominant_kernel_work(prob, args.precision)
+    avg_s = prof_ms / n_launch / 1e3 if n_launch else None
+    gbs = bytes_per / avg_s / 1e9 if avg_s else None
     traffic = None
     if os.path.exists(PROFILE_FILE):
         pf = json.load(open(PROFILE_FILE))
         ent = pf.get(f"cheb_fine_{args.precision}")
         if ent and ent.get("source_hash") == kernel_source_hash():
             traffic = ent.get("dram_bytes_per_launch")
-    roof = dict(bound="hbm", kernel="k_cheb_sell (finest-level Chebyshev step of the V-cycle)",
-                achieved=achieved, peak=peak, unit="GB/s", frac=(achieved / peak) if achieved else None,
-                traffic=traffic, peak_source="measured" if "hbm_gbs" in peaks else "fallback",
-                algorithmic_bytes_per_launch=bytes_per, launches=n_launch,
-                avg_launch_us=1e3 * prof_ms / n_launch if n_launch else None,
-                share_of_step=prof_ms / ms if ms else None)
+    hbm = dict(achieved=gbs, peak=peak, unit="GB/s", frac=(gbs / peak) if gbs else None,
+               peak_source="measured" if "hbm_gbs" in peaks else "fallback")
+    common = dict(kernel="k_cheb_sell (finest-level Chebyshev step of the V-cycle)", traffic=traffic,
+                  algorithmic_bytes_per_launch=bytes_per, algorithmic_flops_per_launch=flops_per,
+                  launches=n_launch, avg_launch_us=1e6 * avg_s if avg_s else None,
+                  share_of_step=prof_ms / ms if ms else None)
+    if args.precision == "fp64":
+        # FP64 arithmetic bounds this kernel on GB300 (FP64 pipe ~80% busy at ~47% of HBM, see
+        # profiles/): report against the measured FP64 rate, with the HBM fraction beside it
+        import torch
+        p64 = fp64_peak_tflops(torch)
+        tf = flops_per / avg_s / 1e12 if avg_s else None
+        roof = dict(bound="alu", achieved=tf, peak=p64, unit="TFLOP/s", frac=(tf / p64) if tf else None,
+                    peak_source="measured FP64 DGEMM 4096^3 in this run", hbm=hbm, **common)
+    else:
+        roof = dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=hbm["frac"],
+                    peak_source=hbm["peak_source"], **common)
     cpu = None
     if not args.no_baseline and world == 1:
         r = run_oracle(3, 1)

@@ -7,9 +7,9 @@
  * time step of Section 3.2 of Benedusi, Ellingsrud, Herlyng and Rognes,
  * "Scalable approximation and solvers for ionic electrodiffusion in cellular
  * geometries" (arXiv 2403.04491). Each step is: membrane update (Section 3.2),
- * assembly of A_{n-1} and f_n (Section 4.1, Eq. 4.2), and the solve of
+ * assembly of A_{n-1} and f_n (Section 4.1, Eq. 4.3), and the solve of
  * A_{n-1} u_n = f_n by flexible GMRES(30) right-preconditioned with one
- * algebraic-multigrid V-cycle on the block-diagonal P_0 (Eq. 4.3, Section 4.2,
+ * algebraic-multigrid V-cycle on the block-diagonal P_0 (Eq. 4.4, Section 4.2,
  * Section 6.2).
  *
  * Conventions shared by every entry point:
@@ -113,7 +113,7 @@ typedef struct {
     double c_i0[KNP_MAX_IONS];       /* uniform initial [k]_i^0 */
     double c_e0[KNP_MAX_IONS];       /* uniform initial [k]_e^0 */
     double phi_M0;                   /* initial membrane potential; phi_i^0 = phi_M0, phi_e^0 = 0 */
-    /* membrane (Eq. 2.9 and the leak model): per facet, in knp_mesh_facets order */
+    /* membrane (Eq. 2.15 and the leak model): per facet, in knp_mesh_facets order */
     const int32_t* facet_model;      /* host [n_facets]: KNP_MODEL_LEAK or KNP_MODEL_HH */
     const double* facet_gleak;       /* host [n_facets * n_ions] leak conductances g_leak^k */
     int32_t ion_na, ion_k;           /* ions carrying the HH Na / K channels and the stimulus (Na) */
@@ -137,7 +137,7 @@ void knp_problem_destroy(knp_problem* prob);
 /* Membrane update and assembly for the current step n (Section 3.2, Section
  * 4.1): from u_{n-1}, w_{n-1} and t_{n-1}, computes w_n by Rush-Larsen with
  * phi_M frozen, the explicit I_ch^{k,n-1}, alpha^{n-1}, C^{n-1}, the values of
- * A_{n-1} in its fixed pattern and f_n (Eq. 4.2), with the point pin of
+ * A_{n-1} in its fixed pattern and f_n (Eq. 4.3), with the point pin of
  * Remark 4.1. Stream-ordered; returns without synchronising. */
 knp_status knp_assemble_step(knp_problem* prob);
 
@@ -152,7 +152,7 @@ typedef struct {
     double p_drop;              /* drop prolongator entries below p_drop x the row's largest (0: keep all) */
 } knp_amg_opts;
 
-/* Smoothed-aggregation AMG on P_0 (Eq. 4.3) assembled from the initial
+/* Smoothed-aggregation AMG on P_0 (Eq. 4.4) assembled from the initial
  * state and reused for every step (Section 4.2). Must follow
  * knp_problem_create and precede knp_solve. Errors: KNP_ERR_INVALID_ARG,
  * KNP_ERR_OOM, KNP_ERR_NUMERIC (singular coarse matrix), KNP_ERR_CUDA. */
@@ -213,13 +213,13 @@ knp_status knp_adjoint_begin(knp_problem* prob);
 /* One reverse step n. Precondition: the problem's state is (u_{n-1}, w_{n-1}, t_{n-1})
  * (restore it with knp_state_set, e.g. from a checkpoint and a recomputed segment). u_n
  * is the forward solution of step n and dLdu_n the loss's partial derivative with
- * respect to u_n, both [n_dof] in the Eq. 4.2 order, in `space`. The call assembles
+ * respect to u_n, both [n_dof] in the Eq. 4.3 order, in `space`. The call assembles
  * A_{n-1}, solves for lambda_n, and updates the carried quantities and the gradient
  * accumulators. The state itself is not changed. Errors: KNP_ERR_STATE (no
  * knp_adjoint_begin or knp_amg_setup), KNP_ERR_NOT_CONVERGED, KNP_ERR_CUDA. */
 knp_status knp_adjoint_step(knp_problem* prob, knp_memspace space, const double* u_n, const double* dLdu_n,
                             const knp_solve_opts* opts, knp_solve_stats* stats);
-/* After the step n = 1: dLdu0 [n_dof] (Eq. 4.2 order; the entries of c_i^k are the
+/* After the step n = 1: dLdu0 [n_dof] (Eq. 4.3 order; the entries of c_i^k are the
  * gradient with respect to the initial intracellular concentrations), dLdw0 [3 *
  * n_membrane_vertices], grad_gleak [n_facets * n_ions], and the last lambda [n_dof].
  * Any pointer may be NULL; buffers in `space`. */
@@ -240,7 +240,7 @@ knp_status knp_state_set(knp_problem* prob, knp_memspace space, const double* c_
 /* implementation; not needed to run a simulation)                            */
 /* ------------------------------------------------------------------------- */
 
-/* Unknown order used by the inspection calls: the paper's Eq. 4.2 order
+/* Unknown order used by the inspection calls: the paper's Eq. 4.3 order
  * [c_i^1..c_i^K, phi_i, c_e^1..c_e^K, phi_e], each block in region node order;
  * n = n_dof. */
 
@@ -250,7 +250,7 @@ knp_status knp_rhs_get(const knp_problem* prob, double* rhs);
 knp_status knp_apply_operator(knp_problem* prob, const double* x, double* y);
 /* y = A_{n-1}^T x with the last assembled operator; x, y host [n]. */
 knp_status knp_apply_operator_transpose(knp_problem* prob, const double* x, double* y);
-/* Entries of A_{n-1}: for each (row, col) pair in the Eq. 4.2 order, the value
+/* Entries of A_{n-1}: for each (row, col) pair in the Eq. 4.3 order, the value
  * (0 where the entry is outside the pattern). rows, cols, vals host [count]. */
 knp_status knp_operator_entries(knp_problem* prob, int64_t count, const int64_t* rows,
                                 const int64_t* cols, double* vals);
@@ -261,7 +261,7 @@ knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* 
  * preconditioner - code running under a CUDA stream capture or while a CUDA graph is being
  * built, hosts that fix their device memory up front, and plugin or embedded hosts that
  * forbid allocation after start-up.
- * r and z are DEVICE pointers to [n_dof] doubles in the same Eq. 4.2 order as
+ * r and z are DEVICE pointers to [n_dof] doubles in the same Eq. 4.3 order as
  * knp_apply_preconditioner, owned by the caller; z = V-cycle(P_0) r with the same kernels
  * and hierarchy, so the result equals knp_apply_preconditioner's. The call allocates
  * nothing: its work vectors live in one static device array of 32 MiB that every GPU which

@@ -190,7 +190,7 @@ def phi_and_grads(F: TorchForm, s_old: system.State, u_new: np.ndarray, lam: np.
 
 
 def probe_matrix(pb: system.Problem, points: np.ndarray) -> sp.csr_matrix:
-    """P1 interpolation of phi_e at points in Omega_e: rows = points, columns = unknowns (Eq. 4.2 order)."""
+    """P1 interpolation of phi_e at points in Omega_e: rows = points, columns = unknowns (Eq. 4.3 order)."""
     t = pb.topo
     coords, elems = pb.coords, pb.elems
     E = elems[t.elems_e]
@@ -215,7 +215,7 @@ def probe_matrix(pb: system.Problem, points: np.ndarray) -> sp.csr_matrix:
 def run_with_adjoint(pb: system.Problem, s0: system.State, n_steps: int, Pmat: sp.csr_matrix):
     """Forward (exact solves) and reverse sweep for L = sum_n sum_p (P u_n)_p^2.
 
-    Returns dict(L, states, grad_gleak (n_f, K), dLdu0 (Eq. 4.2 order), dLdw0)."""
+    Returns dict(L, states, grad_gleak (n_f, K), dLdu0 (Eq. 4.3 order), dLdw0)."""
     F = TorchForm(pb)
     states, mats = [s0], []
     s = s0

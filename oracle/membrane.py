@@ -6,9 +6,9 @@ integrals as P1 functions.
 
 * reversal potential  E_k = RT/(F z_k) ln([k]_e/[k]_i)                      (Section 2.4.1)
 * capacitive split    alpha_r^k = D_r^k z_k^2 [k]_r / sum_l D_r^l z_l^2 [l]_r   (Section 2.2)
-* C_r^k = alpha_r^k C_m / (F z_k)                                            (Eq. 3.5)
+* C_r^k = alpha_r^k C_m / (F z_k)                                            (Eq. 3.6)
 * Hodgkin-Huxley gates by N_ode Rush-Larsen substeps with phi_M frozen at phi_M^{n-1} (Section 3.2)
-* channel driving terms q = G(w) (phi_M - E_k): leak G = 1, HH Na m^3 h, HH K n^4 (Eq. 2.9)
+* channel driving terms q = G(w) (phi_M - E_k): leak G = 1, HH Na m^3 h, HH K n^4 (Eq. 2.15)
 
 The HH-1952 rates are not printed in the paper (Section 2.4.1 cites HH-1952);
 the reading used is the textbook set in the modern sign convention with

@@ -1,5 +1,5 @@
 """The time loop of Section 3.2: for n = 1..N_t, membrane update, assembly of A_{n-1} and f_n,
-and the solve of Eq. 4.2 (exact, or GMRES with x0 = u_{n-1})."""
+and the solve of Eq. 4.3 (exact, or GMRES with x0 = u_{n-1})."""
 from __future__ import annotations
 
 import numpy as np

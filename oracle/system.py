@@ -1,20 +1,20 @@
 """The linearised KNP-EMI system A_{n-1} u_n = f_n and the preconditioner P_0 (Section 4).
 
-Unknown order (Eq. 4.2): [c_i^1 .. c_i^|K|, phi_i, c_e^1 .. c_e^|K|, phi_e], each
+Unknown order (Eq. 4.3): [c_i^1 .. c_i^|K|, phi_i, c_e^1 .. c_e^|K|, phi_e], each
 block in region node order. Blocks follow the matrices A_r^n and B_rq^n of
 Section 4.1 with tau_r^k = dt D_r^k and tau~_r^k = tau_r^k z_k / psi, psi = RT/F.
 
 Readings where the paper is silent or inconsistent (also listed in the design doc):
-  * the bulk source enters the right-hand side multiplied by dt (Eq. 3.4 omits it);
+  * the bulk source enters the right-hand side multiplied by dt (Eq. 3.5 omits it);
   * h_r = +-_r (dt I_ch - C_m phi_M^{n-1}) / F: the printed "+C_m phi_M" contradicts a
-    re-derivation of Eq. 3.6 from Eq. 3.2 with the backward difference of Section 3.2;
+    re-derivation of h_r in Eq. 3.7 from Eq. 3.2 with the backward difference of Section 3.2;
   * alpha and C are nodal P1 on Gamma; int_Gamma C phi_M v is the exact triple product,
     on both sides of the equation;
   * the stimulus conductance is evaluated at t_{n-1} (explicit I_ch);
   * null space: the phi_e row and column of the extracellular node nearest to the origin
     are replaced by the identity with right-hand side 0 (Remark 4.1);
   * P_0 = blockdiag(M_r + tau_r^k A_r, C_m/F M_{r,Gamma} + sum_k z_k tau~_r^k A_r^{k,0}) with the
-    same pin (Eq. 4.3, P_n reused as P_0).
+    same pin (Eq. 4.4, P_n reused as P_0).
 Pinned by tests/test_oracle_system.py (resting steady state, charge conservation,
 species mass balance, zero residual of a manufactured solution, LU(P_0)-GMRES
 iteration counts of Section 6.3).
@@ -168,7 +168,7 @@ def membrane_fields(pb: Problem, s: State):
 
 
 def channel_currents(pb: Problem, mf: dict, t_prev: float) -> np.ndarray:
-    """I_ch^k at the vertices of each facet, shape (n_ions, n_f, m+1) (Eq. 2.9, leak model).
+    """I_ch^k at the vertices of each facet, shape (n_ions, n_f, m+1) (Eq. 2.15 and the leak model).
 
     Facet conductances are piecewise constant; the nodal driving terms are P1.
     """
@@ -262,7 +262,7 @@ def apply_pin(pb: Problem, A: sp.csr_matrix, f: np.ndarray):
 
 
 def preconditioner_P0(pb: Problem, s0: State) -> sp.csr_matrix:
-    """P_0 of Eq. 4.3 (block diagonal over the 2(|K|+1) fields), from the initial state."""
+    """P_0 of Eq. 4.4 (block diagonal over the 2(|K|+1) fields), from the initial state."""
     g = pb.geo
     K = pb.n_ions
     z, psi, dt = pb.z, pb.psi, pb.dt

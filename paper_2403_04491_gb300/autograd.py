@@ -17,7 +17,7 @@ from .knp import Problem
 
 def probe_weights(mesh_coords, elems, tag, nodes_e, N_i, N_e, points):
     """P1 interpolation of phi_e at points inside the extracellular mesh: (index [n_p, d+1]
-    into the Eq. 4.2 unknown vector, weight [n_p, d+1])."""
+    into the Eq. 4.3 unknown vector, weight [n_p, d+1])."""
     ecell = np.nonzero(tag == 0)[0]
     E = elems[ecell]
     x = mesh_coords[E]
@@ -55,7 +55,7 @@ class Simulation:
         self.s0 = s0
         self.gleak0 = None
 
-    # state as one device vector in the Eq. 4.2 order, gates, time
+    # state as one device vector in the Eq. 4.3 order, gates, time
     def _get(self):
         p = self.prob
         Ni, Ne = p.N_i, p.N_e

@@ -1,4 +1,4 @@
-// Smoothed-aggregation hierarchy for the block-diagonal preconditioner P_0 (Eq. 4.3).
+// Smoothed-aggregation hierarchy for the block-diagonal preconditioner P_0 (Eq. 4.4).
 //
 // P_0 has 2(|K|+1) diagonal blocks: per region, M_r + tau_r^k A_r for each ion and
 // C_m/F M_{r,Gamma} + sum_k z_k tau~_r^k A_r^{k,0} for the potential. All blocks of a

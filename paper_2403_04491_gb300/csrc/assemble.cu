@@ -1,5 +1,5 @@
 // Per-step membrane update and assembly of A_{n-1} and f_n (Section 3.2, Section 4.1,
-// Eq. 4.2). Six stream-ordered launches, none of them using atomics:
+// Eq. 4.3). Six stream-ordered launches, none of them using atomics:
 //   membrane_nodes   phi_M, E_k, alpha_r^k, C_r^k, Rush-Larsen gates, channel driving terms
 //   elem_means       element means of [k]^{n-1} (exact weight of A_r^{k,n-1} for P1)
 //   edge_values      A_r^{k,n-1} on each undirected edge: sum over incident elements

@@ -17,7 +17,7 @@ void state_copy_in(knp_problem* p, bool device, const double* c_i, const double*
 
 namespace {
 
-// Eq. 4.2 order <-> interleaved node-major layout
+// Eq. 4.3 order <-> interleaved node-major layout
 int64_t eq42_index(const knp_problem* p, int64_t g, int k) {
     if (g < p->N_i) return (int64_t)k * p->N_i + g;
     return 4 * p->N_i + (int64_t)k * p->N_e + (g - p->N_i);
@@ -143,7 +143,7 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
         KNP_CUDA(cudaStreamSynchronize(st));
         const SellPattern& S = p->sell;
         const int64_t n = p->n_nodes, ne = S.n_entries;
-        // P_0: the field-diagonal blocks of A_0 (Eq. 4.3) on the region-internal pattern
+        // P_0: the field-diagonal blocks of A_0 (Eq. 4.4) on the region-internal pattern
         HostCsr4 A0;
         A0.n_rows = A0.n_cols = n;
         A0.ptr.assign(n + 1, 0);

@@ -229,11 +229,13 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
-// threads per row, a power of two in [1, 32]: enough groups to fill the GPU (about 2 x 152 SMs
-// x 1024 threads) on small coarse levels, and at least two entries per lane
-int pick_tpr(int64_t rows, double mean_len) {
+// threads per row, a power of two: enough groups to fill the GPU (about 2 x 152 SMs x 1024
+// threads) on small coarse levels, and at least four entries per lane. The group reduction costs
+// shuffles and adds of four values per level, which in FP64 run on the slow FP64 pipe, so FP64
+// rows get at most 4 lanes and FP32 rows at most 16.
+int pick_tpr(int64_t rows, double mean_len, int max_tpr) {
     int t = 1;
-    while (t < 32 && (double)rows * t < 311296.0 && t * 4 <= mean_len) t *= 2;
+    while (t < max_tpr && (double)rows * t < 311296.0 && t * 8 <= mean_len) t *= 2;
     return t;
 }
 
@@ -248,7 +250,7 @@ struct DevCsr4 {
     DArray<T> val;
     void upload(const HostCsr4& h, cudaStream_t st) {
         n = h.n_rows;
-        tpr = pick_tpr(n, n ? (double)h.nnz() / (double)n : 1.0);
+        tpr = pick_tpr(n, n ? (double)h.nnz() / (double)n : 1.0, sizeof(T) == 8 ? 4 : 16);
         ptr.upload(h.ptr, st);
         col.upload(h.col, st);
         val.upload(cast_vec<T>(h.val), st);
@@ -532,7 +534,7 @@ __global__ void k_fill(int64_t n, double v, double* __restrict__ out) {
     if (i < n) out[i] = v;
 }
 
-// Eq. 4.2 order [c_i^1..c_i^3, phi_i, c_e^1..c_e^3, phi_e] <-> node-major [node][4]
+// Eq. 4.3 order [c_i^1..c_i^3, phi_i, c_e^1..c_e^3, phi_e] <-> node-major [node][4]
 __global__ void k_eq42_to_nodes(int64_t Ni, int64_t Ne, const double* __restrict__ a, double* __restrict__ out) {
     int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= Ni + Ne) return;

@@ -333,7 +333,7 @@ class Problem:
         _check(_lib.knp_adjoint_begin(self.handle))
 
     def adjoint_step(self, u_n, dLdu_n, rtol=1e-10, restart=30, max_it=1000, phi_e_group=True):
-        """u_n, dLdu_n in the Eq. 4.2 order: numpy arrays (host) or CUDA tensors (device)."""
+        """u_n, dLdu_n in the Eq. 4.3 order: numpy arrays (host) or CUDA tensors (device)."""
         o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
         s = SolveStats()
         if hasattr(u_n, "data_ptr"):
@@ -371,7 +371,7 @@ class Problem:
 
     def apply_preconditioner_noalloc(self, r_dev, z_dev):
         """knp_apply_preconditioner_noalloc on device buffers (torch tensors or raw pointers) in the
-        same Eq. 4.2 order; allocates nothing (work vectors in the library's static device array)."""
+        same Eq. 4.3 order; allocates nothing (work vectors in the library's static device array)."""
         ptr = lambda a: C.c_void_p(a if isinstance(a, int) else a.data_ptr())
         _check(_lib.knp_apply_preconditioner_noalloc(self.handle, ptr(r_dev), ptr(z_dev)))
 
