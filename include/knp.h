@@ -150,6 +150,7 @@ typedef struct {
     double cheb_ratio;          /* lower eigenvalue bound = lambda_max / cheb_ratio */
     double theta_coarse;        /* strength threshold on levels >= 1 (< 0: same as theta) */
     double p_drop;              /* drop prolongator entries below p_drop x the row's largest (0: keep all) */
+    int32_t host_setup;         /* 1: build the hierarchy on the host (reference path); 0: on the GPU */
 } knp_amg_opts;
 
 /* Smoothed-aggregation AMG on P_0 (Eq. 4.4) assembled from the initial

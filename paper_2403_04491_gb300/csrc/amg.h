@@ -12,6 +12,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 namespace knp {
 
 // CSR with four values per entry ([nnz][4], field-major inside an entry).
@@ -51,5 +53,12 @@ struct AmgSetupOpts {
 // (excluded from the field-3 near-null vector), or -1.
 void amg_build(const HostCsr4& A0, const std::vector<double>& strength0, int64_t pin_row,
                const AmgSetupOpts& o, HostHierarchy& H);
+// the same on the GPU (amg_gpu.cu); the coarsest dense inverse stays on the host. Returns false
+// when a row of P exceeds the kernel's fixed capacity (the caller then builds on the host).
+bool amg_build_gpu(const HostCsr4& A0, const std::vector<double>& strength0, int64_t pin_row,
+                   const AmgSetupOpts& o, HostHierarchy& H, cudaStream_t st,
+                   void (*host_spgemm)(const HostCsr4&, const HostCsr4&, HostCsr4&));
+void amg_host_spgemm(const HostCsr4& A, const HostCsr4& B, HostCsr4& C);
+void amg_coarse_inverse(HostHierarchy& H);
 
 }  // namespace knp

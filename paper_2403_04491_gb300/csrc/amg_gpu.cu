@@ -1,0 +1,792 @@
+// GPU construction of the smoothed-aggregation hierarchy on P_0 (Section 4.2: one AMG V-cycle
+// on P_0, set up once). The same algorithm as the host version in amg_setup.cpp, step for
+// step, so that both give the same aggregates and operators:
+//   strength graph  |s_ij| >= theta sqrt(|s_ii s_jj|)                  k_strength_count/fill
+//   MIS-2           Luby-style rounds with hashed priorities: a node is a root when it holds
+//                   the largest priority among undecided nodes within distance 2, and is
+//                   excluded when a root lies within distance 2             k_mis2_*
+//   aggregates      roots + their strong neighbours; leftovers join the first aggregated strong
+//                   neighbour; what remains becomes singletons               k_agg_*
+//   prolongator     P_f = (I - omega_f D_f^-1 A_f) P_tent,f, four fields on one pattern
+//   Galerkin        R = P^T, A_c = R (A P) per field by a row-per-warp SpGEMM: keys through a
+//                   shared-memory hash, values accumulated in the host's (Gustavson) order, so
+//                   the result does not depend on thread timing               k_spgemm_*
+//   Chebyshev bounds power iteration on D^-1 A per field, 20 steps             k_power_*
+// The coarsest level's dense inverse is formed on the host (a few hundred unknowns).
+#include <algorithm>
+#include <cmath>
+
+#include "amg.h"
+#include "problem.h"
+
+namespace knp {
+
+namespace {
+
+inline unsigned nb(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+__host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// ------------------------------------------------------------------ exclusive scan (int64)
+__global__ void k_scan_block(int64_t n, const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                             int64_t* __restrict__ sums) {
+    __shared__ int64_t sh[1024];
+    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    int64_t v = i < n ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = sh[threadIdx.x] - v;   // exclusive
+    if (threadIdx.x == 1023) sums[blockIdx.x] = sh[1023];
+}
+
+__global__ void k_scan_add(int64_t n, int64_t* __restrict__ out, const int64_t* __restrict__ offs) {
+    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    if (i < n) out[i] += offs[blockIdx.x];
+}
+
+// out[0..n] = exclusive scan of in[0..n-1] with out[n] = total; returns the total
+int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
+    if (n == 0) {
+        int64_t z = 0;
+        KNP_CUDA(cudaMemcpyAsync(out, &z, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        KNP_CUDA(cudaStreamSynchronize(st));
+        return 0;
+    }
+    int64_t blocks = (n + 1023) / 1024;
+    DArray<int64_t> sums;
+    sums.alloc(blocks);
+    k_scan_block<<<(unsigned)blocks, 1024, 0, st>>>(n, in, out, sums.p);
+    const int64_t* total_src = sums.p;   // one block: its sum is the total
+    DArray<int64_t> offs;
+    if (blocks > 1) {
+        // scan of the block sums (recursion ends at one block), then the block offsets
+        offs.alloc(blocks + 1);
+        exclusive_scan(sums.p, offs.p, blocks, st);
+        k_scan_add<<<(unsigned)blocks, 1024, 0, st>>>(n, out, offs.p);
+        total_src = offs.p + blocks;
+    }
+    KNP_CUDA(cudaMemcpyAsync(out + n, total_src, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    int64_t total = 0;
+    KNP_CUDA(cudaMemcpyAsync(&total, total_src, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    KNP_CUDA(cudaStreamSynchronize(st));
+    return total;
+}
+
+// ------------------------------------------------------------------ level basics
+struct DCsr4 {
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    DArray<int64_t> ptr;
+    DArray<int32_t> col;
+    DArray<double> val;
+};
+
+// diagonal, D^-1 (with an empty field row given a unit diagonal, as on the host), |s_ii|
+__global__ void k_diag(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                       double* __restrict__ val, const double* __restrict__ s, double* __restrict__ dinv,
+                       double* __restrict__ sdiag, int* __restrict__ bad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t td = -1;
+    for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t)
+        if (col[t] == i) td = t;
+    if (td < 0) {
+        atomicExch(bad, 1);
+        return;
+    }
+    sdiag[i] = fabs(s ? s[td] : val[4 * td + 3]);   // before the empty-row fix, as on the host
+    for (int f = 0; f < 4; ++f) {
+        double d = val[4 * td + f];
+        if (d == 0.0) {
+            bool empty = true;
+            for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) empty &= val[4 * t + f] == 0.0;
+            if (empty) val[4 * td + f] = d = 1.0;
+        }
+        if (!(d > 0.0) || !isfinite(d)) atomicExch(bad, 2);
+        dinv[4 * i + f] = 1.0 / d;
+    }
+}
+
+__global__ void k_power_init(int64_t n4, double* __restrict__ x) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n4) x[i] = 1.0 + 0.5 * ((hash32((uint32_t)i) & 1023) / 1023.0);
+}
+
+// y = D^-1 A x per field; partial sums of |y|^2 and |x|^2 per field
+__global__ void k_power_step(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ dinv,
+                             const double* __restrict__ x, double* __restrict__ y, double* __restrict__ partial) {
+    __shared__ double sh[8][256];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s[4] = {0, 0, 0, 0};
+        for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t)
+            for (int f = 0; f < 4; ++f) s[f] += val[4 * t + f] * x[4 * (int64_t)col[t] + f];
+        for (int f = 0; f < 4; ++f) {
+            double v = dinv[4 * i + f] * s[f];
+            y[4 * i + f] = v;
+            acc[f] += v * v;
+            acc[4 + f] += x[4 * i + f] * x[4 * i + f];
+        }
+    }
+    for (int k = 0; k < 8; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int k = 0; k < 8; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partial[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_power_scale(int64_t n4, int nblocks, const double* __restrict__ partial, const double* __restrict__ y,
+                              double* __restrict__ x, double* __restrict__ lam) {
+    __shared__ double tot[8];
+    if (threadIdx.x < 8) {
+        double s = 0;
+        for (int b = 0; b < nblocks; ++b) s += partial[b * 8 + threadIdx.x];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x < 4)
+        lam[threadIdx.x] = sqrt(tot[threadIdx.x] / fmax(tot[4 + threadIdx.x], 1e-300));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = y[i] * (1.0 / sqrt(fmax(tot[i & 3], 1e-300)));
+}
+
+// ------------------------------------------------------------------ strength graph
+__global__ void k_strength_count(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ s, const double* __restrict__ sdiag, double theta,
+                                 int64_t* __restrict__ cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t c = 0;
+    for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+        int64_t j = col[t];
+        if (j == i) continue;
+        if (fabs(s[t]) >= theta * sqrt(sdiag[i] * sdiag[j]) && s[t] != 0.0) ++c;
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_strength_fill(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ s, const double* __restrict__ sdiag, double theta,
+                                const int64_t* __restrict__ gptr, int32_t* __restrict__ gadj) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t q = gptr[i];
+    for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+        int64_t j = col[t];
+        if (j == i) continue;
+        if (fabs(s[t]) >= theta * sqrt(sdiag[i] * sdiag[j]) && s[t] != 0.0) gadj[q++] = (int32_t)j;
+    }
+}
+
+// ------------------------------------------------------------------ MIS-2
+__device__ __forceinline__ uint64_t mis_key(uint8_t st, uint64_t prio) {
+    return st == 0 ? prio : (st == 1 ? ~0ULL : 0ULL);
+}
+
+__global__ void k_mis2_init(int64_t n, int level, const int64_t* __restrict__ gptr, uint8_t* __restrict__ state,
+                            uint64_t* __restrict__ prio) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    prio[i] = ((uint64_t)hash32((uint32_t)i * 2654435761u + (uint32_t)level * 97u) << 32) | (uint64_t)i;
+    state[i] = (gptr[i] == gptr[i + 1]) ? 1 : 0;   // isolated nodes are singleton roots
+}
+
+__global__ void k_mis2_max1(int64_t n, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gadj,
+                            const uint8_t* __restrict__ state, const uint64_t* __restrict__ prio,
+                            uint64_t* __restrict__ m1) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t v = mis_key(state[i], prio[i]);
+    for (int64_t t = gptr[i]; t < gptr[i + 1]; ++t) {
+        int64_t j = gadj[t];
+        v = max(v, mis_key(state[j], prio[j]));
+    }
+    m1[i] = v;
+}
+
+__global__ void k_mis2_max2(int64_t n, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gadj,
+                            const uint64_t* __restrict__ m1, uint64_t* __restrict__ m2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t v = m1[i];
+    for (int64_t t = gptr[i]; t < gptr[i + 1]; ++t) v = max(v, m1[gadj[t]]);
+    m2[i] = v;
+}
+
+__global__ void k_mis2_update(int64_t n, const uint64_t* __restrict__ m2, const uint64_t* __restrict__ prio,
+                              uint8_t* __restrict__ state, unsigned long long* __restrict__ undecided) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != 0) return;
+    if (m2[i] == prio[i])
+        state[i] = 1;
+    else if (m2[i] == ~0ULL)
+        state[i] = 2;
+    else
+        atomicAdd(undecided, 1ULL);
+}
+
+__global__ void k_flag(int64_t n, const uint8_t* __restrict__ state, uint8_t v, int64_t* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = state[i] == v ? 1 : 0;
+}
+
+__global__ void k_root_ids(int64_t n, const uint8_t* __restrict__ state, const int64_t* __restrict__ rank,
+                           int32_t* __restrict__ agg) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) agg[i] = state[i] == 1 ? (int32_t)rank[i] : -1;
+}
+
+__global__ void k_root_neighbours(int64_t n, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gadj,
+                                  const uint8_t* __restrict__ state, int32_t* __restrict__ agg) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != 1) return;
+    // neighbourhoods of roots are disjoint (roots are at distance >= 3)
+    for (int64_t t = gptr[i]; t < gptr[i + 1]; ++t) agg[gadj[t]] = agg[i];
+}
+
+__global__ void k_leftover(int64_t n, const int64_t* __restrict__ gptr, const int32_t* __restrict__ gadj,
+                           const int32_t* __restrict__ agg_old, int32_t* __restrict__ agg_new, int* __restrict__ changed) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t a = agg_old[i];
+    if (a < 0) {
+        for (int64_t t = gptr[i]; t < gptr[i + 1]; ++t) {
+            int32_t b = agg_old[gadj[t]];
+            if (b >= 0) {
+                a = b;
+                *changed = 1;
+                break;
+            }
+        }
+    }
+    agg_new[i] = a;
+}
+
+__global__ void k_unassigned(int64_t n, const int32_t* __restrict__ agg, int64_t* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = agg[i] < 0 ? 1 : 0;
+}
+
+__global__ void k_singletons(int64_t n, int64_t base, const int64_t* __restrict__ rank, int32_t* __restrict__ agg) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && agg[i] < 0) agg[i] = (int32_t)(base + rank[i]);
+}
+
+// ------------------------------------------------------------------ smoothed prolongator
+constexpr int PMAX = 96;    // distinct aggregates in one row of P (rows beyond: host fallback)
+
+// Row i of P: slots in order of first appearance (agg(i), then the aggregates of row i of A),
+// accumulated in that order as on the host, then sorted by column; pass 0 counts, pass 1 writes.
+__global__ void k_prolong(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const double* __restrict__ dinv,
+                          const double* __restrict__ B, const int32_t* __restrict__ agg, double om0, double om1,
+                          double om2, double om3, double p_drop, int pass, int64_t* __restrict__ cnt,
+                          const int64_t* __restrict__ pptr, int32_t* __restrict__ pcol, double* __restrict__ pval,
+                          int* __restrict__ overflow) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double om[4] = {om0, om1, om2, om3};
+    int32_t keys[PMAX];
+    double acc[PMAX][4];
+    int m = 0;
+    auto slot = [&](int32_t c) -> int {
+        for (int q = 0; q < m; ++q)
+            if (keys[q] == c) return q;
+        if (m >= PMAX) return -1;
+        keys[m] = c;
+        for (int f = 0; f < 4; ++f) acc[m][f] = 0.0;
+        return m++;
+    };
+    int q0 = slot(agg[i]);
+    for (int f = 0; f < 4; ++f) acc[q0][f] += B[4 * i + f];
+    for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+        int64_t j = col[t];
+        int q = slot(agg[j]);
+        if (q < 0) {
+            atomicExch(overflow, 1);
+            return;
+        }
+        for (int f = 0; f < 4; ++f) acc[q][f] -= om[f] * dinv[4 * i + f] * val[4 * t + f] * B[4 * j + f];
+    }
+    // sort slots by column (insertion sort on a permutation)
+    int order[PMAX];
+    for (int q = 0; q < m; ++q) {
+        int k = q;
+        while (k > 0 && keys[order[k - 1]] > keys[q]) {
+            order[k] = order[k - 1];
+            --k;
+        }
+        order[k] = q;
+    }
+    double rmax[4] = {0, 0, 0, 0};
+    for (int q = 0; q < m; ++q)
+        for (int f = 0; f < 4; ++f) rmax[f] = fmax(rmax[f], fabs(acc[q][f]));
+    int64_t w = pass ? pptr[i] : 0;
+    int64_t c = 0;
+    for (int k = 0; k < m; ++k) {
+        int q = order[k];
+        bool keep = keys[q] == agg[i] || p_drop <= 0;
+        for (int f = 0; f < 4 && !keep; ++f) keep = fabs(acc[q][f]) >= p_drop * rmax[f];
+        if (!keep) continue;
+        if (pass) {
+            pcol[w + c] = keys[q];
+            for (int f = 0; f < 4; ++f) pval[4 * (w + c) + f] = acc[q][f];
+        }
+        ++c;
+    }
+    if (!pass) cnt[i] = c;
+}
+
+__global__ void k_coarse_B(int64_t n, const int32_t* __restrict__ agg, const double* __restrict__ B,
+                           unsigned long long* __restrict__ Bc_bits) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // max over aggregate members; B >= 0, so the IEEE bit patterns order like the values
+    for (int f = 0; f < 4; ++f)
+        atomicMax(&Bc_bits[4 * (int64_t)agg[i] + f], (unsigned long long)__double_as_longlong(B[4 * i + f]));
+}
+
+// ------------------------------------------------------------------ transpose
+__global__ void k_col_count(int64_t nnz, const int32_t* __restrict__ col, unsigned long long* __restrict__ cnt) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < nnz) atomicAdd(&cnt[col[t]], 1ULL);
+}
+
+__global__ void k_transpose_fill(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, const int64_t* __restrict__ rptr,
+                                 unsigned long long* __restrict__ fill, int32_t* __restrict__ rcol,
+                                 double* __restrict__ rval) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t t = ptr[i]; t < ptr[i + 1]; ++t) {
+        int64_t c = col[t];
+        int64_t q = rptr[c] + (int64_t)atomicAdd(&fill[c], 1ULL);
+        rcol[q] = (int32_t)i;
+        for (int f = 0; f < 4; ++f) rval[4 * q + f] = val[4 * t + f];
+    }
+}
+
+// sort each row of a CSR4 by column (rows are short)
+__global__ void k_sort_rows(int64_t n, const int64_t* __restrict__ ptr, int32_t* __restrict__ col,
+                            double* __restrict__ val) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t a = ptr[i] + 1; a < ptr[i + 1]; ++a) {
+        int32_t c = col[a];
+        double v[4] = {val[4 * a], val[4 * a + 1], val[4 * a + 2], val[4 * a + 3]};
+        int64_t b = a;
+        while (b > ptr[i] && col[b - 1] > c) {
+            col[b] = col[b - 1];
+            for (int f = 0; f < 4; ++f) val[4 * b + f] = val[4 * (b - 1) + f];
+            --b;
+        }
+        col[b] = c;
+        for (int f = 0; f < 4; ++f) val[4 * b + f] = v[f];
+    }
+}
+
+// ------------------------------------------------------------------ SpGEMM C = A B (four fields)
+// One warp per row of C. The keys of the row go through an open-addressing hash set in shared
+// memory (capacity hcap, at most hcap/2 keys), are compacted and bitonic-sorted. In the value
+// pass the entries of row i of A are taken one after another (the host's order) and the lanes
+// share the entries of the matching row of B, whose keys are distinct, so each output slot
+// receives its terms in the same order as on the host and no atomics are needed.
+__device__ __forceinline__ int hash_insert(int32_t* table, int hcap, int32_t key, int* count) {
+    uint32_t h = hash32((uint32_t)key) & (hcap - 1);
+    while (true) {
+        int32_t prev = atomicCAS(&table[h], -1, key);
+        if (prev == -1) {
+            atomicAdd(count, 1);
+            return (int)h;
+        }
+        if (prev == key) return (int)h;
+        h = (h + 1) & (hcap - 1);
+    }
+}
+
+__device__ void warp_bitonic_sort(int32_t* a, int m, int lane) {
+    // a[0..m) padded to the next power of two with INT_MAX by the caller
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < m; i += 32) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    int32_t x = a[i], y = a[l];
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// keys of row `row` of C into sorted[0..count); returns count (or -1 on overflow)
+__device__ int row_keys(int64_t row, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
+                        const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol, int32_t* table,
+                        int32_t* sorted, int hcap, int* count, int lane) {
+    for (int h = lane; h < hcap; h += 32) table[h] = -1;
+    if (lane == 0) *count = 0;
+    __syncwarp();
+    for (int64_t t = aptr[row]; t < aptr[row + 1]; ++t) {
+        int64_t k = acol[t];
+        for (int64_t u = bptr[k] + lane; u < bptr[k + 1]; u += 32) {
+            if (*count < hcap / 2) hash_insert(table, hcap, bcol[u], count);
+        }
+        __syncwarp();
+        if (*count >= hcap / 2) return -1;
+    }
+    __syncwarp();
+    int m = *count;
+    // compact
+    __shared__ int cpos[32];
+    if (lane == 0) cpos[threadIdx.x / 32] = 0;
+    __syncwarp();
+    for (int h = lane; h < hcap; h += 32) {
+        int32_t key = table[h];
+        if (key >= 0) sorted[atomicAdd(&cpos[threadIdx.x / 32], 1)] = key;
+    }
+    __syncwarp();
+    int p2 = 1;
+    while (p2 < m) p2 <<= 1;
+    for (int i = m + lane; i < p2; i += 32) sorted[i] = 0x7fffffff;
+    __syncwarp();
+    warp_bitonic_sort(sorted, p2, lane);
+    return m;
+}
+
+__global__ void k_spgemm_count(int64_t n, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
+                               const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol, int hcap,
+                               int64_t* __restrict__ cnt, int* __restrict__ overflow) {
+    extern __shared__ int32_t smem[];
+    const int wib = threadIdx.x / 32, lane = threadIdx.x % 32, wpb = blockDim.x / 32;
+    int32_t* table = smem + (int64_t)wib * (2 * hcap + 1);
+    int32_t* sorted = table + hcap;
+    int* count = sorted + hcap;
+    int64_t row = (int64_t)blockIdx.x * wpb + wib;
+    if (row >= n) return;
+    int m = row_keys(row, aptr, acol, bptr, bcol, table, sorted, hcap, count, lane);
+    if (lane == 0) {
+        if (m < 0) atomicExch(overflow, 1);
+        cnt[row] = m < 0 ? 0 : m;
+    }
+}
+
+__global__ void k_spgemm_fill(int64_t n, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
+                              const double* __restrict__ aval, const int64_t* __restrict__ bptr,
+                              const int32_t* __restrict__ bcol, const double* __restrict__ bval, int hcap,
+                              const int64_t* __restrict__ cptr, int32_t* __restrict__ ccol,
+                              double* __restrict__ cval) {
+    extern __shared__ int32_t smem[];
+    const int wib = threadIdx.x / 32, lane = threadIdx.x % 32, wpb = blockDim.x / 32;
+    int32_t* table = smem + (int64_t)wib * (2 * hcap + 1);
+    int32_t* sorted = table + hcap;
+    int* count = sorted + hcap;
+    int64_t row = (int64_t)blockIdx.x * wpb + wib;
+    if (row >= n) return;
+    int m = row_keys(row, aptr, acol, bptr, bcol, table, sorted, hcap, count, lane);
+    if (m < 0) return;
+    const int64_t base = cptr[row];
+    double* out = cval + 4 * base;
+    for (int q = lane; q < m; q += 32) {
+        ccol[base + q] = sorted[q];
+        for (int f = 0; f < 4; ++f) out[4 * q + f] = 0.0;
+    }
+    __syncwarp();
+    for (int64_t t = aptr[row]; t < aptr[row + 1]; ++t) {
+        int64_t k = acol[t];
+        double a[4] = {aval[4 * t], aval[4 * t + 1], aval[4 * t + 2], aval[4 * t + 3]};
+        for (int64_t u = bptr[k] + lane; u < bptr[k + 1]; u += 32) {
+            int32_t key = bcol[u];
+            int lo = 0, hi = m - 1;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (sorted[mid] < key)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            for (int f = 0; f < 4; ++f) out[4 * lo + f] += a[f] * bval[4 * u + f];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_row_bound(int64_t n, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
+                            const int64_t* __restrict__ bptr, unsigned long long* __restrict__ maxb) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long b = 0;
+    for (int64_t t = aptr[i]; t < aptr[i + 1]; ++t) b += bptr[acol[t] + 1] - bptr[acol[t]];
+    atomicMax(maxb, b);
+}
+
+void download(const DCsr4& d, HostCsr4& h, cudaStream_t st) {
+    h.n_rows = d.n_rows;
+    h.n_cols = d.n_cols;
+    d.ptr.download(h.ptr, st);
+    d.col.download(h.col, st);
+    d.val.download(h.val, st);
+    KNP_CUDA(cudaStreamSynchronize(st));
+}
+
+void upload(const HostCsr4& h, DCsr4& d, cudaStream_t st) {
+    d.n_rows = h.n_rows;
+    d.n_cols = h.n_cols;
+    d.nnz = h.nnz();
+    d.ptr.upload(h.ptr, st);
+    d.col.upload(h.col, st);
+    d.val.upload(h.val, st);
+}
+
+// C = A B on the device; false if a row overflowed the shared-memory hash (caller falls back)
+bool spgemm_gpu(const DCsr4& A, const DCsr4& B, DCsr4& C, cudaStream_t st) {
+    const int64_t n = A.n_rows;
+    DArray<unsigned long long> maxb;
+    maxb.alloc(1);
+    maxb.zero(st);
+    k_row_bound<<<nb(n, 256), 256, 0, st>>>(n, A.ptr.p, A.col.p, B.ptr.p, maxb.p);
+    unsigned long long bound = 0;
+    KNP_CUDA(cudaMemcpyAsync(&bound, maxb.p, sizeof(bound), cudaMemcpyDeviceToHost, st));
+    KNP_CUDA(cudaStreamSynchronize(st));
+    int64_t want = (int64_t)std::min<unsigned long long>(bound, (unsigned long long)B.n_cols);
+    int hcap = 64;
+    while (hcap < 2 * want + 2 && hcap < 8192) hcap <<= 1;
+    const int wpb = hcap <= 1024 ? 4 : 1;
+    const size_t smem = (size_t)wpb * (2 * hcap + 1) * sizeof(int32_t);
+    if (smem > 48 * 1024) {
+        KNP_CUDA(cudaFuncSetAttribute(k_spgemm_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KNP_CUDA(cudaFuncSetAttribute(k_spgemm_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    DArray<int64_t> cnt;
+    DArray<int> ovf;
+    cnt.alloc(n);
+    ovf.alloc(1);
+    ovf.zero(st);
+    const unsigned grid = (unsigned)((n + wpb - 1) / wpb);
+    k_spgemm_count<<<grid, 32 * wpb, smem, st>>>(n, A.ptr.p, A.col.p, B.ptr.p, B.col.p, hcap, cnt.p, ovf.p);
+    int of = 0;
+    KNP_CUDA(cudaMemcpyAsync(&of, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KNP_CUDA(cudaStreamSynchronize(st));
+    if (of) return false;
+    C.n_rows = n;
+    C.n_cols = B.n_cols;
+    C.ptr.alloc(n + 1);
+    C.nnz = exclusive_scan(cnt.p, C.ptr.p, n, st);
+    C.col.alloc(std::max<int64_t>(1, C.nnz));
+    C.val.alloc(std::max<int64_t>(1, 4 * C.nnz));
+    k_spgemm_fill<<<grid, 32 * wpb, smem, st>>>(n, A.ptr.p, A.col.p, A.val.p, B.ptr.p, B.col.p, B.val.p, hcap,
+                                                C.ptr.p, C.col.p, C.val.p);
+    KNP_CUDA(cudaGetLastError());
+    return true;
+}
+
+}  // namespace
+
+// Device version of amg_build (same algorithm and output as the host one, see amg_setup.cpp).
+bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, int64_t pin_row,
+                   const AmgSetupOpts& o, HostHierarchy& H, cudaStream_t st, void (*host_spgemm)(const HostCsr4&,
+                   const HostCsr4&, HostCsr4&)) {
+    H.levels.clear();
+    auto A = std::make_unique<DCsr4>();
+    upload(A0h, *A, st);
+    DArray<double> s;
+    s.upload(strength0, st);
+    DArray<double> B;
+    {
+        std::vector<double> b(4 * A0h.n_rows, 1.0);
+        if (pin_row >= 0) b[4 * pin_row + 3] = 0.0;
+        B.upload(b, st);
+    }
+    DArray<int> flag;
+    flag.alloc(1);
+    for (int lev = 0;; ++lev) {
+        const int64_t n = A->n_rows;
+        H.levels.emplace_back();
+        HostLevel& L = H.levels.back();
+        // diagonal, D^-1, Chebyshev bounds
+        DArray<double> dinv, sdiag;
+        dinv.alloc(4 * n);
+        sdiag.alloc(n);
+        flag.zero(st);
+        k_diag<<<nb(n, 256), 256, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, lev == 0 ? s.p : nullptr, dinv.p,
+                                            sdiag.p, flag.p);
+        int bad = 0;
+        KNP_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KNP_CUDA(cudaStreamSynchronize(st));
+        KNP_REQUIRE(bad == 0, KNP_ERR_NUMERIC, "P_0 hierarchy: %s on level %d",
+                    bad == 1 ? "missing diagonal" : "non-positive diagonal", lev);
+        {
+            DArray<double> x, y, partial, lam;
+            x.alloc(4 * n);
+            y.alloc(4 * n);
+            const int pb = (int)std::min<int64_t>(1024, nb(n, 256));
+            partial.alloc(8 * pb);
+            lam.alloc(4);
+            k_power_init<<<nb(4 * n, 256), 256, 0, st>>>(4 * n, x.p);
+            for (int it = 0; it < 20; ++it) {
+                k_power_step<<<pb, 256, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, dinv.p, x.p, y.p, partial.p);
+                k_power_scale<<<pb, 256, 0, st>>>(4 * n, pb, partial.p, y.p, x.p, lam.p);
+            }
+            double rho[4];
+            KNP_CUDA(cudaMemcpyAsync(rho, lam.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            KNP_CUDA(cudaStreamSynchronize(st));
+            for (int f = 0; f < 4; ++f) {
+                L.lmax[f] = 1.1 * rho[f];
+                L.lmin[f] = L.lmax[f] / o.cheb_ratio;
+            }
+        }
+        dinv.download(L.dinv, st);
+        download(*A, L.A, st);
+        if (n <= o.coarse_max || lev + 1 >= o.max_levels) break;
+        // strength graph (level 0: the given scalar; coarser: the potential field)
+        const double theta = (lev == 0 || o.theta_coarse < 0) ? o.theta : o.theta_coarse;
+        DArray<double> sc;
+        const double* sv = s.p;
+        if (lev > 0) {
+            std::vector<double> hs(A->nnz);
+            for (int64_t t = 0; t < A->nnz; ++t) hs[t] = L.A.val[4 * t + 3];
+            sc.upload(hs, st);
+            sv = sc.p;
+        }
+        DArray<int64_t> cnt, gptr;
+        DArray<int32_t> gadj;
+        cnt.alloc(n);
+        gptr.alloc(n + 1);
+        k_strength_count<<<nb(n, 256), 256, 0, st>>>(n, A->ptr.p, A->col.p, sv, sdiag.p, theta, cnt.p);
+        int64_t ne = exclusive_scan(cnt.p, gptr.p, n, st);
+        gadj.alloc(std::max<int64_t>(1, ne));
+        k_strength_fill<<<nb(n, 256), 256, 0, st>>>(n, A->ptr.p, A->col.p, sv, sdiag.p, theta, gptr.p, gadj.p);
+        // MIS-2 rounds
+        DArray<uint8_t> state;
+        DArray<uint64_t> prio, m1, m2;
+        DArray<unsigned long long> und;
+        state.alloc(n);
+        prio.alloc(n);
+        m1.alloc(n);
+        m2.alloc(n);
+        und.alloc(1);
+        k_mis2_init<<<nb(n, 256), 256, 0, st>>>(n, lev, gptr.p, state.p, prio.p);
+        for (int round = 0; round < 1000; ++round) {
+            und.zero(st);
+            k_mis2_max1<<<nb(n, 256), 256, 0, st>>>(n, gptr.p, gadj.p, state.p, prio.p, m1.p);
+            k_mis2_max2<<<nb(n, 256), 256, 0, st>>>(n, gptr.p, gadj.p, m1.p, m2.p);
+            k_mis2_update<<<nb(n, 256), 256, 0, st>>>(n, m2.p, prio.p, state.p, und.p);
+            unsigned long long u = 0;
+            KNP_CUDA(cudaMemcpyAsync(&u, und.p, sizeof(u), cudaMemcpyDeviceToHost, st));
+            KNP_CUDA(cudaStreamSynchronize(st));
+            if (u == 0) break;
+        }
+        // aggregates
+        DArray<int64_t> fl, rank;
+        fl.alloc(n);
+        rank.alloc(n + 1);
+        k_flag<<<nb(n, 256), 256, 0, st>>>(n, state.p, 1, fl.p);
+        int64_t na = exclusive_scan(fl.p, rank.p, n, st);
+        DArray<int32_t> agg, agg2;
+        agg.alloc(n);
+        agg2.alloc(n);
+        k_root_ids<<<nb(n, 256), 256, 0, st>>>(n, state.p, rank.p, agg.p);
+        k_root_neighbours<<<nb(n, 256), 256, 0, st>>>(n, gptr.p, gadj.p, state.p, agg.p);
+        for (int pass = 0; pass < 8; ++pass) {
+            flag.zero(st);
+            k_leftover<<<nb(n, 256), 256, 0, st>>>(n, gptr.p, gadj.p, agg.p, agg2.p, flag.p);
+            std::swap(agg.p, agg2.p);
+            int ch = 0;
+            KNP_CUDA(cudaMemcpyAsync(&ch, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            KNP_CUDA(cudaStreamSynchronize(st));
+            if (!ch) break;
+        }
+        k_unassigned<<<nb(n, 256), 256, 0, st>>>(n, agg.p, fl.p);
+        int64_t extra = exclusive_scan(fl.p, rank.p, n, st);
+        k_singletons<<<nb(n, 256), 256, 0, st>>>(n, na, rank.p, agg.p);
+        na += extra;
+        if (na >= n || na == 0 || (double)na > 0.85 * (double)n) break;
+        // smoothed prolongator
+        double om[4];
+        for (int f = 0; f < 4; ++f) om[f] = (4.0 / 3.0) / (L.lmax[f] / 1.1);
+        DCsr4 P;
+        P.n_rows = n;
+        P.n_cols = na;
+        P.ptr.alloc(n + 1);
+        flag.zero(st);
+        k_prolong<<<nb(n, 64), 64, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, dinv.p, B.p, agg.p, om[0], om[1], om[2],
+                                            om[3], o.p_drop, 0, cnt.p, nullptr, nullptr, nullptr, flag.p);
+        int of = 0;
+        KNP_CUDA(cudaMemcpyAsync(&of, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KNP_CUDA(cudaStreamSynchronize(st));
+        if (of) return false;   // a row of P with more than PMAX aggregates: the caller uses the host build
+        P.nnz = exclusive_scan(cnt.p, P.ptr.p, n, st);
+        P.col.alloc(P.nnz);
+        P.val.alloc(4 * P.nnz);
+        k_prolong<<<nb(n, 64), 64, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, dinv.p, B.p, agg.p, om[0], om[1], om[2],
+                                            om[3], o.p_drop, 1, nullptr, P.ptr.p, P.col.p, P.val.p, flag.p);
+        // R = P^T
+        DCsr4 R;
+        R.n_rows = na;
+        R.n_cols = n;
+        R.nnz = P.nnz;
+        {
+            DArray<unsigned long long> cc, fill;
+            cc.alloc(na);
+            cc.zero(st);
+            fill.alloc(na);
+            fill.zero(st);
+            k_col_count<<<nb(P.nnz, 256), 256, 0, st>>>(P.nnz, P.col.p, cc.p);
+            DArray<int64_t> cc64;
+            cc64.alloc(na);
+            KNP_CUDA(cudaMemcpyAsync(cc64.p, cc.p, na * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+            R.ptr.alloc(na + 1);
+            exclusive_scan(cc64.p, R.ptr.p, na, st);
+            R.col.alloc(R.nnz);
+            R.val.alloc(4 * R.nnz);
+            k_transpose_fill<<<nb(n, 256), 256, 0, st>>>(n, P.ptr.p, P.col.p, P.val.p, R.ptr.p, fill.p, R.col.p,
+                                                         R.val.p);
+            k_sort_rows<<<nb(na, 128), 128, 0, st>>>(na, R.ptr.p, R.col.p, R.val.p);
+        }
+        download(P, L.P, st);
+        download(R, L.R, st);
+        // coarse near-null vectors
+        DArray<unsigned long long> Bc;
+        Bc.alloc(4 * na);
+        Bc.zero(st);
+        k_coarse_B<<<nb(n, 256), 256, 0, st>>>(n, agg.p, B.p, Bc.p);
+        // Galerkin product
+        auto AP = std::make_unique<DCsr4>();
+        auto Ac = std::make_unique<DCsr4>();
+        bool ok = spgemm_gpu(*A, P, *AP, st) && spgemm_gpu(R, *AP, *Ac, st);
+        if (!ok) {
+            HostCsr4 hAP, hAc;
+            host_spgemm(L.A, L.P, hAP);
+            host_spgemm(L.R, hAP, hAc);
+            upload(hAc, *Ac, st);
+        }
+        B.alloc(4 * na);
+        KNP_CUDA(cudaMemcpyAsync(B.p, Bc.p, 4 * na * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        A = std::move(Ac);
+        KNP_CUDA(cudaGetLastError());
+    }
+    // dense inverse of the coarsest operator on the host
+    amg_coarse_inverse(H);
+    return true;
+}
+
+}  // namespace knp

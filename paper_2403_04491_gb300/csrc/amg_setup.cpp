@@ -353,6 +353,12 @@ void amg_build(const HostCsr4& A0, const std::vector<double>& strength0, int64_t
         H.levels.emplace_back();
         H.levels[lev + 1].A = std::move(Ac);
     }
+    amg_coarse_inverse(H);
+}
+
+void amg_host_spgemm(const HostCsr4& A, const HostCsr4& B, HostCsr4& C) { spgemm4(A, B, C); }
+
+void amg_coarse_inverse(HostHierarchy& H) {
     // dense inverse of the coarsest operator, per field
     HostLevel& Lc = H.levels.back();
     const int64_t nc = Lc.A.n_rows;

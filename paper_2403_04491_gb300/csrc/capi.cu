@@ -184,7 +184,8 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
         }
         HostHierarchy H;
         AmgSetupOpts so{o->theta, o->coarse_max, o->max_levels, o->cheb_ratio, o->theta_coarse, o->p_drop};
-        amg_build(A0, strength, p->pin, so, H);
+        if (o->host_setup || !amg_build_gpu(A0, strength, p->pin, so, H, st, amg_host_spgemm))
+            amg_build(A0, strength, p->pin, so, H);
         amg_upload(p, H, o->precision, o->cheb_degree);
         KNP_CUDA(cudaMemcpyAsync(p->svec.p, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         KNP_CUDA(cudaMemcpyAsync(p->sinv.p, si.data(), si.size() * sizeof(double), cudaMemcpyHostToDevice, st));

@@ -58,7 +58,7 @@ class ProblemDesc(C.Structure):
 class AmgOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("theta", C.c_double), ("coarse_max", C.c_int32),
                 ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("cheb_ratio", C.c_double),
-                ("theta_coarse", C.c_double), ("p_drop", C.c_double)]
+                ("theta_coarse", C.c_double), ("p_drop", C.c_double), ("host_setup", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -261,8 +261,9 @@ class Problem:
         _check(_lib.knp_assemble_step(self.handle))
 
     def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=2,
-                  cheb_ratio=10.0, theta_coarse=0.0, p_drop=0.0):
-        o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop)
+                  cheb_ratio=10.0, theta_coarse=0.0, p_drop=0.0, host_setup=False):
+        o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop,
+                    int(host_setup))
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
     def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):

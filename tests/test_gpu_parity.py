@@ -138,3 +138,24 @@ def test_state_roundtrip_and_resume():
     for k in ("c_i", "phi_i", "c_e", "phi_e", "w"):
         np.testing.assert_array_equal(end_a[k], end_b[k])
     assert end_a["t"] == end_b["t"]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_gpu_amg_setup_matches_host_setup(precision):
+    """The GPU hierarchy construction (MIS-2, smoothed P, SpGEMM) gives the host's hierarchy: same
+    level sizes and patterns, the same V-cycle to rounding, the same FGMRES iterations."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2).with_nx(24)
+    _, a = problem_from_config(cfg)
+    a.amg_setup(precision=precision, host_setup=True)
+    _, b = problem_from_config(cfg)
+    b.amg_setup(precision=precision, host_setup=False)
+    ia, ib = a.amg_info(), b.amg_info()
+    assert ia["nodes"] == ib["nodes"] and ia["nnz"] == ib["nnz"], (ia, ib)
+    r = np.random.default_rng(9).standard_normal(a.n_dof)
+    za, zb = a.apply_preconditioner(r), b.apply_preconditioner(r)
+    tol = 1e-10 if precision == 0 else 1e-5
+    assert np.linalg.norm(za - zb) <= tol * np.linalg.norm(za)
+    sa = a.step(2, rtol=1e-10)
+    sb = b.step(2, rtol=1e-10)
+    assert [s["iterations"] for s in sa] == [s["iterations"] for s in sb]
