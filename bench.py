@@ -45,7 +45,23 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="workload: 2 (default, the headline), 1 (2D leak), 3 (125-cell 3D, FP32 hierarchy, "
+                         "rtol 1e-8), 4 (16-cell 2D)")
+    ap.add_argument("--nx", type=int, default=None, help="override the mesh resolution of the workload")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time a checkpointed forward + adjoint run of the 16-cell 2D workload (KNPFunction)")
+    args = ap.parse_args()
+    if args.config == 3 and "--precision" not in sys.argv:
+        args.precision = "fp32"
+    if args.config == 3 and "--rtol" not in sys.argv:
+        args.rtol = 1e-8
+    return args
+
+
+def workload_name(cfg, n_dof):
+    return (f"{cfg.name}: {cfg.dim}D, {cfg.nx}^{cfg.dim} mesh, {len(cfg.cell_lo)} cell(s), {n_dof:,} DOF, "
+            f"dt {cfg.dt * 1e3:g} ms, {'HH' if cfg.model == 1 else 'leak'} membrane")
 
 
 # --------------------------------------------------------------------------- oracle legs
@@ -239,7 +255,9 @@ def ours(args):
     from paper_2403_04491_gb300 import problem_from_config
     from synth import make_config
 
-    cfg = make_config(2)
+    cfg = make_config(args.config)
+    if args.nx:
+        cfg = cfg.with_nx(args.nx)
     prec = 0 if args.precision == "fp64" else 1
     t0 = time.perf_counter()
     mesh, prob = problem_from_config(cfg)
@@ -248,6 +266,8 @@ def ours(args):
     prob.amg_setup(precision=prec)
     t_amg = time.perf_counter() - t0
     n_dof = prob.n_dof
+    free, total = torch.cuda.mem_get_info()
+    mem_gb = (total - free) / 1e9
     for _ in range(args.warmup):
         prob.step(1, rtol=args.rtol)
     torch.cuda.synchronize()
@@ -255,8 +275,12 @@ def ours(args):
         dist.barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ms, iters, launches, prof = measure(prob, torch, args.steps, args.rtol, kernel_class=1)
+    ms, iters, launches, _ = measure(prob, torch, args.steps, args.rtol)
     clocks = sampler.stop()
+    # the dominant kernel, timed by per-launch CUDA events on its stream over a second pass of the
+    # same number of steps (event pairs go around single launches, so the V-cycle is not replayed
+    # from its CUDA graph in this pass)
+    _, _, _, prof = measure(prob, torch, args.steps, args.rtol, kernel_class=1)
     if world > 1:
         dist.barrier()
         t = torch.tensor([ms], device="cuda")
@@ -267,8 +291,9 @@ def ours(args):
     # end to end through the public API with host buffers: per step the state goes host->device,
     # one knp_step runs, and the new state comes back device->host (pinned host memory)
     e2e = None if args.no_e2e else e2e_run(prob, torch, args, n_dof, world)
-    mixed = None if args.no_mixed else mixed_run(cfg, mesh, torch, args, n_dof)
-    report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg)
+    mixed = None if (args.no_mixed or args.config != 2) else mixed_run(cfg, mesh, torch, args, n_dof)
+    report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg,
+           workload_name(cfg, n_dof), mem_gb)
 
 
 def e2e_run(prob, torch, args, n_dof, world):
@@ -335,7 +360,8 @@ def mixed_run(cfg, mesh, torch, args, n_dof):
     return mixed
 
 
-def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg):
+def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg,
+           workload=WORKLOAD, mem_gb=None):
     import numpy as np
     import torch.distributed as dist
     value = n_dof * args.steps * world / (ms / 1e3)
@@ -374,27 +400,72 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
         roof = dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=hbm["frac"],
                     peak_source=hbm["peak_source"], **common)
     cpu = None
-    if not args.no_baseline and world == 1:
+    if not args.no_baseline and world == 1 and args.config == 2:
         r = run_oracle(3, 1)
         v = r["n_dof"] * len(r["times"]) / sum(r["times"])
         cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=oracle_sample_desc(SAMPLE_NX, 3))
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64" if args.precision == "fp64" else "f64 (FGMRES) / f32 (AMG)", data="synthetic",
-                config=dict(workload=WORKLOAD, n_dof=n_dof, l2="working set per step > L2 (operator, hierarchy and "
+                config=dict(workload=workload, n_dof=n_dof, l2="working set per step > L2 (operator, hierarchy and "
                                                                "Krylov basis exceed 129 MB); no flush",
                             precision=args.precision, rtol=args.rtol, restart=30,
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 iters_per_step=float(np.mean(iters)), iters=iters, setup_s=dict(create=t_create, amg=t_amg),
                 amg=prob.amg_info(), gpu_launches=launches, clocks=clocks, roofline=roof,
+                device_memory_gb=mem_gb,
                 e2e=e2e, cpu_baseline=cpu, mixed=mixed)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
+def adjoint_bench(args):
+    """Forward run with checkpoints every 20 steps, then the reverse sweep (recompute + adjoint
+    steps), on the differentiation workload; reports both rates and the gradient sizes."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_04491_gb300 import KNPFunction, Simulation, problem_from_config, probe_weights
+    from synth import make_config
+    from synth.configs import probe_points
+    cfg = make_config(4)
+    if args.nx:
+        cfg = cfg.with_nx(args.nx)
+    n_steps = args.steps if "--steps" in sys.argv else cfg.n_steps
+    mesh, prob = problem_from_config(cfg)
+    prob.amg_setup()
+    m = cfg.mesh
+    ni, ne = mesh.nodes()
+    idx, w = probe_weights(m.coords, m.elems, m.elem_tag, ne, prob.N_i, prob.N_e, probe_points(cfg))
+    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=args.rtol)
+    gK = torch.tensor(prob._facet_gleak[:, 1].copy(), requires_grad=True)
+    cK = torch.tensor(sim.s0["c_i"][1].copy(), requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    traces = KNPFunction.apply(gK, cK, sim)
+    loss = (traces ** 2).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    line = dict(metric="DOF*timesteps/s, forward and checkpointed adjoint", unit="DOF*steps/s", impl="ours",
+                config=dict(workload=workload_name(cfg, prob.n_dof) + f", {n_steps} steps, checkpoint every 20, "
+                            "loss = sum of phi_e^2 at 64 probes", n_dof=prob.n_dof, rtol=args.rtol),
+                forward=dict(seconds=t1 - t0, value=prob.n_dof * n_steps / (t1 - t0)),
+                adjoint=dict(seconds=t2 - t1, value=prob.n_dof * n_steps / (t2 - t1),
+                             note="includes recomputing every segment from its checkpoint"),
+                loss=float(loss), grad_gK_norm=float(gK.grad.norm()), grad_cK_norm=float(cK.grad.norm()))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.adjoint:
+        adjoint_bench(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

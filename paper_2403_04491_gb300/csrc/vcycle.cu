@@ -9,6 +9,7 @@
 // groups of TPR threads per row (TPR a power of two chosen from the mean row length),
 // so that the short, wide coarse levels still fill the GPU.
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -283,6 +284,11 @@ struct AmgDev {
 };
 
 AmgHierarchy::~AmgHierarchy() {
+    for (auto& kv : graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (gstream) cudaStreamDestroy(gstream);
     delete static_cast<AmgDev<double>*>(h64);
     delete static_cast<AmgDev<float>*>(h32);
 }
@@ -375,6 +381,7 @@ void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degre
     p->amg = new AmgHierarchy();
     p->amg->precision = precision;
     p->amg->levels = (int)H.levels.size();
+    p->amg->use_graphs = std::getenv("KNP_NO_GRAPHS") == nullptr;
     for (const HostLevel& L : H.levels) {
         p->amg->nodes.push_back(L.A.n_rows);
         p->amg->nnz.push_back(L.A.nnz());
@@ -469,11 +476,7 @@ static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, Pr
     smooth(L, D.coef[l], D.degree, false, nullptr, nullptr, pr, l == 0, st);
 }
 
-// z = V-cycle(P_0)(s .* v); v, s, z are [n][4] doubles on the device.
-void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
-    KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
-    cudaStream_t st = p->stream;
-    ProfScope ps(&p->prof, KC_VCYCLE, st);
+static void vcycle_launch(knp_problem* p, const double* v, const double* s, double* z, cudaStream_t st) {
     if (p->amg->h32) {
         auto& D = *static_cast<AmgDev<float>*>(p->amg->h32);
         vcycle_rec(D, 0, v, s, &p->prof, st);
@@ -484,7 +487,56 @@ void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
         vcycle_rec(D, 0, v, s, &p->prof, st);
         KNP_CUDA(cudaMemcpyAsync(z, D.L[0]->x.p, 4 * D.L[0]->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    KNP_CUDA(cudaGetLastError());
+}
+
+// z = V-cycle(P_0)(s .* v); v, s, z are [n][4] doubles on the device. The V-cycle is a fixed
+// sequence of about 25 launches, so it is captured once per (v, s, z) into a CUDA graph and
+// replayed on a private stream ordered after the caller's stream. Each replay starts from
+// scratch (the first kernel writes b, x and d of the finest level), so replays are independent.
+// While a kernel class is being profiled the launches go out one by one.
+void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
+    KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
+    AmgHierarchy& H = *p->amg;
+    cudaStream_t st = p->stream;
+    if (!H.use_graphs || p->prof.active >= 0) {
+        ProfScope ps(&p->prof, KC_VCYCLE, st);
+        vcycle_launch(p, v, s, z, st);
+        KNP_CUDA(cudaGetLastError());
+        return;
+    }
+    if (!H.gstream) {
+        KNP_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
+        KNP_CUDA(cudaEventCreateWithFlags(&H.ev_in, cudaEventDisableTiming));
+        KNP_CUDA(cudaEventCreateWithFlags(&H.ev_out, cudaEventDisableTiming));
+    }
+    auto key = std::make_tuple(v, s, z);
+    auto it = H.graphs.find(key);
+    if (it == H.graphs.end()) {
+        VcycleGraph g;
+        int64_t before = g_launches.load();
+        KNP_CUDA(cudaStreamBeginCapture(H.gstream, cudaStreamCaptureModeThreadLocal));
+        try {
+            vcycle_launch(p, v, s, z, H.gstream);
+        } catch (...) {
+            cudaGraph_t tmp;
+            cudaStreamEndCapture(H.gstream, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            throw;
+        }
+        cudaGraph_t graph = nullptr;
+        KNP_CUDA(cudaStreamEndCapture(H.gstream, &graph));
+        g.launches = (int)(g_launches.load() - before);
+        g_launches.fetch_sub(g.launches);
+        KNP_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+        cudaGraphDestroy(graph);
+        it = H.graphs.emplace(key, g).first;
+    }
+    KNP_CUDA(cudaEventRecord(H.ev_in, st));
+    KNP_CUDA(cudaStreamWaitEvent(H.gstream, H.ev_in, 0));
+    KNP_CUDA(cudaGraphLaunch(it->second.exec, H.gstream));
+    KNP_CUDA(cudaEventRecord(H.ev_out, H.gstream));
+    KNP_CUDA(cudaStreamWaitEvent(st, H.ev_out, 0));
+    count_launch(it->second.launches);
 }
 
 }  // namespace knp
