@@ -160,11 +160,13 @@ typedef struct {
 knp_status knp_amg_setup(knp_problem* prob, const knp_amg_opts* opts);
 
 typedef struct {
-    double rtol;       /* on the preconditioned residual: ||S M^-1 r||_g <= rtol max(||S x_0||_g,
-                          ||S (x - x_0)||_g) for the concentration part and the potential part g,
-                          S^2 = diag(P_0), M^-1 = one V-cycle on P_0, x_0 = u_{n-1} (the paper's
+    double rtol;       /* on the preconditioned residual: ||S M^-1 r||_g <= rtol max(||S x_c||_g,
+                          ||S (x - x_c)||_g) for the concentration part and the potential part g,
+                          S^2 = diag(P_0), M^-1 = one V-cycle on P_0, x_c = the iterate the current
+                          restart cycle began from (the first: x_0 = u_{n-1}) (the paper's
                           preconditioned test, Section 6.2, in the scaled norm, relative to the
-                          initial guess or, for a cold start, to the computed correction) */
+                          iterate or, for a cold start, to the computed correction); with
+                          phi_e_group the phi_e part is floored at 1e-14 ||S phi|| */
     int32_t restart;   /* 30 (Section 6.2) */
     int32_t max_it;    /* total iterations */
     int32_t phi_e_group;  /* 1: test the extracellular potentials as a third group (phi_e is some 1e-8

@@ -9,9 +9,10 @@
 // is classical Gram-Schmidt with one reorthogonalisation (CGS2) in three fused passes.
 //
 // Stopping test: the preconditioned residual, as in Section 6.2, measured in the scaled
-// norm and relative to the initial guess (or, if that is smaller, to the correction of the
-// current cycle, which covers a cold start), for the concentrations and the potentials apart:
-// ||S M^-1 r_k||_g <= rtol max(||S x_0||_g, ||S (x_k - x_0)||_g) for g in {c, phi}. A residual norm
+// norm and relative to the iterate x_c the current restart cycle began from (x_0 for the
+// first cycle; or, if that is smaller, to the correction of the cycle, which covers a cold
+// start), for the concentrations and the potentials apart:
+// ||S M^-1 r_k||_g <= rtol max(||S x_c||_g, ||S (x_k - x_c)||_g) for g in {c, phi}. A residual norm
 // alone is blind to the per-cell constant of phi_i (the intracellular potential block is
 // singular up to the small membrane mass), while M^-1 r approximates the error. For the
 // FGMRES iterate, M^-1 r_k = Z_{k+1} c with c = Q_k^T g_k e_{k+1} from the Givens rotations,
@@ -21,6 +22,8 @@
 // The host sees one Hessenberg column and one Gram row per iteration.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "gmres.h"
 #include "problem.h"
@@ -279,27 +282,37 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     cudaStream_t st = p->stream;
     const int64_t n4 = g.n4;
     const unsigned nb = (unsigned)((n4 + 255) / 256);
-    // reference norms ||S x_0|| of the stopping test, concentrations and potentials apart
-    count_launch(3);
     const int NG = o.phi_e_group ? 3 : 2;
     const int64_t n4i = 4 * p->N_i;
-    if (NG == 3)
-        k_mdot_split<0, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
-    else
-        k_mdot_split<0, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
-    k_reduce<<<NG, 256, 0, st>>>(g.partial.p, RED_BLOCKS, NG, g.dots.p + 2 * MAXV);
-    double xn2[3] = {0, 0, 0};
-    KNP_CUDA(cudaMemcpyAsync(xn2, g.dots.p + 2 * MAXV, NG * sizeof(double), cudaMemcpyDeviceToHost, st));
-    KNP_CUDA(cudaStreamSynchronize(st));
-    KNP_REQUIRE(std::isfinite(xn2[0]) && std::isfinite(xn2[1]) && std::isfinite(xn2[2]), KNP_ERR_NUMERIC,
-                "initial guess is not finite");
+    // reference norms of the stopping test, per group: ||S x|| of the iterate a cycle starts from
+    // (the initial guess, then each restart's), taken together with the cycle's correction
+    double tol[3] = {0, 0, 0};
+    auto reference_norms = [&]() {
+        count_launch(2);
+        if (NG == 3)
+            k_mdot_split<0, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
+        else
+            k_mdot_split<0, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
+        k_reduce<<<NG, 256, 0, st>>>(g.partial.p, RED_BLOCKS, NG, g.dots.p + 2 * MAXV);
+        double xn2[3] = {0, 0, 0};
+        KNP_CUDA(cudaMemcpyAsync(xn2, g.dots.p + 2 * MAXV, NG * sizeof(double), cudaMemcpyDeviceToHost, st));
+        KNP_CUDA(cudaStreamSynchronize(st));
+        KNP_REQUIRE(std::isfinite(xn2[0]) && std::isfinite(xn2[1]) && std::isfinite(xn2[2]), KNP_ERR_NUMERIC,
+                    "iterate is not finite");
+        for (int q = 0; q < NG; ++q) tol[q] = o.rtol * std::sqrt(std::max(xn2[q], 0.0));
+        if (NG == 3) {
+            // phi_e is some 1e-8 of phi_i: below ~1e-14 of the whole potential the rounding of the
+            // coupled equations sets the floor, and a tighter request would stagnate
+            tol[2] = std::max(tol[2], 1e-14 * std::sqrt(std::max(xn2[1] + xn2[2], 0.0)));
+        }
+    };
     k_scale_copy<<<nb, 256, 0, st>>>(n4, fvec, p->sinv.p, g.tmp.p);
     count_launch();
     const double bnorm = std::sqrt(norm2_dev(g, g.tmp.p, st));
     KNP_REQUIRE(std::isfinite(bnorm), KNP_ERR_NUMERIC, "right-hand side is not finite");
     knp_status_detail res{KNP_OK, 0, 0, 0.0};
-    double tol[3];
-    for (int q = 0; q < NG; ++q) tol[q] = o.rtol * std::sqrt(std::max(xn2[q], 0.0));
+    // KNP_GMRES_MONITOR set: every iteration prints the stopping test's terms to stderr
+    static const bool monitor = std::getenv("KNP_GMRES_MONITOR") != nullptr;
     const int m1 = m + 1;
     std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), G(NG * m1 * m1);
     int its = 0, restarts = 0;
@@ -316,6 +329,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         }
         if (its >= o.max_it) break;
         if (its > 0) restarts++;
+        reference_norms();
         count_launch();
         k_scale_inplace<<<nb, 256, 0, st>>>(n4, g.V.p, 1.0 / beta);
         std::fill(gv.begin(), gv.end(), 0.0);
@@ -380,6 +394,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                     yk[i] = sacc / H[i * m + i];
                 }
                 bool ok = true;
+                if (monitor) std::fprintf(stderr, "fgmres%s it %d |g| %.3e", transpose ? "^T" : "", its, std::fabs(gv[k]));
                 for (int q = 0; q < NG; ++q) {
                     double est2 = 0, corr2 = 0;
                     for (int a = 0; a <= k; ++a)
@@ -389,7 +404,11 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                     KNP_REQUIRE(std::isfinite(est2), KNP_ERR_NUMERIC, "preconditioned residual is not finite");
                     const double ref = std::max(tol[q], o.rtol * std::sqrt(std::max(corr2, 0.0)));
                     ok &= std::sqrt(std::max(est2, 0.0)) <= ref;
+                    if (monitor)
+                        std::fprintf(stderr, "  [%d] est %.3e (raw %.2e) tol %.3e corr %.3e", q,
+                                     std::sqrt(std::max(est2, 0.0)), est2, tol[q], std::sqrt(std::max(corr2, 0.0)));
                 }
+                if (monitor) std::fprintf(stderr, "\n");
                 if (ok) {
                     converged = true;
                     k_done = j;

@@ -260,8 +260,8 @@ class Problem:
     def assemble_step(self):
         _check(_lib.knp_assemble_step(self.handle))
 
-    def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=2,
-                  cheb_ratio=10.0, theta_coarse=0.0, p_drop=0.0, host_setup=False):
+    def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=1,
+                  cheb_ratio=4.0, theta_coarse=0.0, p_drop=0.0, host_setup=False):
         o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop,
                     int(host_setup))
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
