@@ -40,16 +40,40 @@ constexpr int MAXW = 3 * MAXV;    // partial-sum slots per block
 
 // Every kernel below is instantiated for a compile-time vector count NV, so that the
 // accumulators and basis values stay in registers (a runtime count put them on the stack).
+
+// One halving step of a warp reduce-scatter of C values per lane (C even): lanes with bit O
+// set keep the upper half and receive their partner's upper half, the others the lower half.
+template <int C>
+__device__ __forceinline__ void warp_halve(double* v, int lane, int O) {
+    const bool hi = (lane & O) != 0;
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) {
+        const double send = hi ? v[k] : v[k + C / 2];
+        const double keep = hi ? v[k + C / 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
+// Block sums of NT values per thread into partial[blockIdx.x][0..NT). Inside a warp the NT
+// values (padded to C, a multiple of 32) are reduce-scattered in five halving steps, which
+// leave lane L with the warp sums of values [L C/32, (L+1) C/32): about C shuffles and adds
+// per lane instead of 5 NT for a butterfly per value (the adds are FP64, the scarce pipe).
 template <int NT>
 __device__ __forceinline__ void block_reduce_store(const double (&acc)[NT], double* __restrict__ partial) {
-    __shared__ double sh[RED_THREADS / 32][NT];
+    constexpr int C = (NT + 31) / 32 * 32;
+    constexpr int PER = C / 32;
+    __shared__ double sh[RED_THREADS / 32][C];
     const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    double v[C];
 #pragma unroll
-    for (int k = 0; k < NT; ++k) {
-        double v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[wid][k] = v;
-    }
+    for (int k = 0; k < C; ++k) v[k] = k < NT ? acc[k] : 0.0;
+    warp_halve<C>(v, lane, 16);
+    warp_halve<C / 2>(v, lane, 8);
+    warp_halve<C / 4>(v, lane, 4);
+    warp_halve<C / 8>(v, lane, 2);
+    warp_halve<C / 16>(v, lane, 1);
+#pragma unroll
+    for (int m = 0; m < PER; ++m) sh[wid][lane * PER + m] = v[m];
     __syncthreads();
     if (threadIdx.x < NT) {
         double s = 0;

@@ -6,8 +6,10 @@
 //
 // Layouts: the finest operator (about 15 entries per row in 3D) is sliced-ELL with one
 // thread per row; coarser operators and the transfer operators are CSR processed by
-// groups of TPR threads per row (TPR a power of two chosen from the mean row length),
-// so that the short, wide coarse levels still fill the GPU.
+// groups of 4 x S threads per row, one thread per (field, entry slot): each thread does one
+// multiply-add per entry and the group reduces one value per field over its S slots (S a
+// power of two chosen from the mean row length), so that the short, wide coarse levels
+// still fill the GPU without spending the slow FP64 pipe on four-value reductions.
 #include <cmath>
 #include <cstdlib>
 #include <map>
@@ -69,22 +71,39 @@ __device__ __forceinline__ void sell_row(int64_t r, const int64_t* __restrict__ 
     }
 }
 
-// Row product of a CSR operator by a group of TPR lanes; every lane of the group gets the sum.
-// Every lane of the warp must call this (the shuffles use the full mask); rows r >= n pass
-// active = false and contribute nothing.
-template <class T, int TPR>
-__device__ __forceinline__ void csr_row(bool active, int64_t r, int lane, const int64_t* __restrict__ ptr,
-                                        const int32_t* __restrict__ col, const T* __restrict__ val,
-                                        const T* __restrict__ x, T acc[4]) {
-    acc[0] = acc[1] = acc[2] = acc[3] = T(0);
-    const int64_t t0 = active ? ptr[r] + lane : 0, t1 = active ? ptr[r + 1] : 0;
-    for (int64_t t = t0; t < t1; t += TPR) {
-        V4<T> a = V4<T>::load(val + 4 * t);
-        V4<T> xv = V4<T>::load(x + 4 * (int64_t)col[t]);
-        for (int f = 0; f < 4; ++f) acc[f] += a.v[f] * xv.v[f];
+// Field f of a CSR row product, by a group of 4 x S lanes (lane = 4 x slot + f): slot k takes
+// entries k, k + S, ... of the row, and the S partial sums of each field are combined by
+// shuffles (and, for S > 8, across the row's warps through shared memory); every lane of the
+// group gets its field's sum. Blocks are 128 threads. Every thread of the block must call this
+// (full-mask shuffles, and a block barrier for S > 8); rows r >= n pass active = false and
+// contribute nothing.
+template <class T, int S>
+__device__ __forceinline__ T csr_row_field(bool active, int64_t r, int slot, int f, const int64_t* __restrict__ ptr,
+                                           const int32_t* __restrict__ col, const T* __restrict__ val,
+                                           const T* __restrict__ x) {
+    static_assert(S >= 1 && S <= 32 && (S & (S - 1)) == 0, "slots: a power of two up to 32");
+    T acc = T(0);
+    if (active) {
+        const int64_t t1 = ptr[r + 1];
+        for (int64_t t = ptr[r] + slot; t < t1; t += S) acc += val[4 * t + f] * x[4 * (int64_t)col[t] + f];
     }
-    for (int o = TPR / 2; o > 0; o >>= 1)
-        for (int f = 0; f < 4; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o, TPR);
+    constexpr int SW = S < 8 ? S : 8;   // slots of the row inside one warp
+    for (int o = 2 * SW; o >= 4; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, 4 * SW);
+    if constexpr (S > 8) {
+        constexpr int NW = S / 8;   // warps per row
+        __shared__ T part[4][4];    // [warp of the block][field]
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) < 4) part[w][threadIdx.x & 31] = acc;
+        __syncthreads();
+        const int w0 = w - w % NW;
+        acc = T(0);
+        for (int k = 0; k < NW; ++k) acc += part[w0 + k][f];
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double pick4(const double c[4], int f) {
+    return f == 0 ? c[0] : f == 1 ? c[1] : f == 2 ? c[2] : c[3];
 }
 
 // first Chebyshev step from x = 0: d = c2 D^-1 b, x = d. On the finest level b = s .* v (double input).
@@ -135,18 +154,22 @@ __global__ void __launch_bounds__(128) k_cheb_sell(int64_t n, const int64_t* __r
     cheb_update<T>(i, acc, x_in, b, dinv, c, d, x_out);
 }
 
-template <class T, int TPR>
+template <class T, int S>
 __global__ void __launch_bounds__(128) k_cheb_csr(int64_t n, const int64_t* __restrict__ ptr,
                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
                                                   const T* __restrict__ x_in, const T* __restrict__ b,
                                                   const T* __restrict__ dinv, Coef4 c, T* __restrict__ d,
                                                   T* __restrict__ x_out) {
     int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-    int64_t i = g / TPR;
-    int lane = (int)(g % TPR);
-    T acc[4];
-    csr_row<T, TPR>(i < n, i, lane, ptr, col, val, x_in, acc);
-    if (lane == 0 && i < n) cheb_update<T>(i, acc, x_in, b, dinv, c, d, x_out);
+    int64_t i = g / (4 * S);
+    int lane = (int)(g % (4 * S)), f = lane & 3;
+    T acc = csr_row_field<T, S>(i < n, i, lane >> 2, f, ptr, col, val, x_in);
+    if (lane < 4 && i < n) {
+        const int64_t k = 4 * i + f;
+        T dd = (T)pick4(c.c1, f) * d[k] + (T)pick4(c.c2, f) * dinv[k] * (b[k] - acc);
+        d[k] = dd;
+        x_out[k] = x_in[k] + dd;
+    }
 }
 
 template <class T>
@@ -163,42 +186,30 @@ __global__ void __launch_bounds__(128) k_resid_sell(int64_t n, const int64_t* __
     bb.store(r + 4 * i);
 }
 
-template <class T, int TPR>
+template <class T, int S>
 __global__ void __launch_bounds__(128) k_resid_csr(int64_t n, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
                                                    const T* __restrict__ x, const T* __restrict__ b,
                                                    T* __restrict__ r) {
     int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-    int64_t i = g / TPR;
-    int lane = (int)(g % TPR);
-    T acc[4];
-    csr_row<T, TPR>(i < n, i, lane, ptr, col, val, x, acc);
-    if (lane == 0 && i < n) {
-        V4<T> bb = V4<T>::load(b + 4 * i);
-        for (int f = 0; f < 4; ++f) bb.v[f] -= acc[f];
-        bb.store(r + 4 * i);
-    }
+    int64_t i = g / (4 * S);
+    int lane = (int)(g % (4 * S)), f = lane & 3;
+    T acc = csr_row_field<T, S>(i < n, i, lane >> 2, f, ptr, col, val, x);
+    if (lane < 4 && i < n) r[4 * i + f] = b[4 * i + f] - acc;
 }
 
 // y[i] (+)= (M x)[i] for a CSR with four values per entry (restriction and prolongation)
-template <class T, int TPR>
+template <class T, int S>
 __global__ void __launch_bounds__(128) k_csr4(int64_t n, const int64_t* __restrict__ ptr,
                                               const int32_t* __restrict__ col, const T* __restrict__ val,
                                               const T* __restrict__ x, T* __restrict__ y, int accumulate) {
     int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-    int64_t i = g / TPR;
-    int lane = (int)(g % TPR);
-    T acc[4];
-    csr_row<T, TPR>(i < n, i, lane, ptr, col, val, x, acc);
-    if (lane == 0 && i < n) {
-        V4<T> yy;
-        if (accumulate) {
-            yy = V4<T>::load(y + 4 * i);
-            for (int f = 0; f < 4; ++f) yy.v[f] += acc[f];
-        } else {
-            for (int f = 0; f < 4; ++f) yy.v[f] = acc[f];
-        }
-        yy.store(y + 4 * i);
+    int64_t i = g / (4 * S);
+    int lane = (int)(g % (4 * S)), f = lane & 3;
+    T acc = csr_row_field<T, S>(i < n, i, lane >> 2, f, ptr, col, val, x);
+    if (lane < 4 && i < n) {
+        const int64_t k = 4 * i + f;
+        y[k] = accumulate ? y[k] + acc : acc;
     }
 }
 
@@ -230,14 +241,12 @@ std::vector<T> cast_vec(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
-// threads per row, a power of two: enough groups to fill the GPU (about 2 x 152 SMs x 1024
-// threads) on small coarse levels, and at least four entries per lane. The group reduction costs
-// shuffles and adds of four values per level, which in FP64 run on the slow FP64 pipe, so FP64
-// rows get at most 4 lanes and FP32 rows at most 16.
-int pick_tpr(int64_t rows, double mean_len, int max_tpr) {
-    int t = 1;
-    while (t < max_tpr && (double)rows * t < 311296.0 && t * 8 <= mean_len) t *= 2;
-    return t;
+// entry slots per row, a power of two up to 32 (4 x S threads per row): doubled while the grid
+// stays within about two waves of 152 SMs x 2048 threads and each slot keeps at least two entries
+int pick_slots(int64_t rows, double mean_len) {
+    int sl = 1;
+    while (sl < 32 && (double)rows * 4 * (2 * sl) <= 622592.0 && 4 * sl <= mean_len) sl *= 2;
+    return sl;
 }
 
 }  // namespace
@@ -245,13 +254,13 @@ int pick_tpr(int64_t rows, double mean_len, int max_tpr) {
 template <class T>
 struct DevCsr4 {
     int64_t n = 0;
-    int tpr = 1;
+    int slots = 1;
     DArray<int64_t> ptr;
     DArray<int32_t> col;
     DArray<T> val;
     void upload(const HostCsr4& h, cudaStream_t st) {
         n = h.n_rows;
-        tpr = pick_tpr(n, n ? (double)h.nnz() / (double)n : 1.0, sizeof(T) == 8 ? 4 : 16);
+        slots = pick_slots(n, n ? (double)h.nnz() / (double)n : 1.0);
         ptr.upload(h.ptr, st);
         col.upload(h.col, st);
         val.upload(cast_vec<T>(h.val), st);
@@ -398,14 +407,14 @@ void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degre
     KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 
-#define KNP_TPR_DISPATCH(tpr, KERNEL, grid_rows, ...)                                                      \
-    switch (tpr) {                                                                                         \
-        case 1: KERNEL<T, 1><<<nblk((grid_rows) * 1, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
-        case 2: KERNEL<T, 2><<<nblk((grid_rows) * 2, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
-        case 4: KERNEL<T, 4><<<nblk((grid_rows) * 4, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
-        case 8: KERNEL<T, 8><<<nblk((grid_rows) * 8, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
-        case 16: KERNEL<T, 16><<<nblk((grid_rows) * 16, 128), 128, 0, st>>>(__VA_ARGS__); break;          \
-        default: KERNEL<T, 32><<<nblk((grid_rows) * 32, 128), 128, 0, st>>>(__VA_ARGS__); break;          \
+#define KNP_SLOT_DISPATCH(slots, KERNEL, grid_rows, ...)                                                   \
+    switch (slots) {                                                                                       \
+        case 1: KERNEL<T, 1><<<nblk((grid_rows) * 4, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
+        case 2: KERNEL<T, 2><<<nblk((grid_rows) * 8, 128), 128, 0, st>>>(__VA_ARGS__); break;             \
+        case 4: KERNEL<T, 4><<<nblk((grid_rows) * 16, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
+        case 8: KERNEL<T, 8><<<nblk((grid_rows) * 32, 128), 128, 0, st>>>(__VA_ARGS__); break;            \
+        case 16: KERNEL<T, 16><<<nblk((grid_rows) * 64, 128), 128, 0, st>>>(__VA_ARGS__); break;          \
+        default: KERNEL<T, 32><<<nblk((grid_rows) * 128, 128), 128, 0, st>>>(__VA_ARGS__); break;         \
     }
 
 template <class T>
@@ -417,7 +426,7 @@ static void cheb_step(DevLevel<T>& L, const Coef4& c, Profiler* pr, bool fine, c
                                                        L.d.p, L.x2.p);
     } else {
         ProfScope ps(fine ? pr : nullptr, KC_CHEB_FINE, st);
-        KNP_TPR_DISPATCH(L.A.tpr, k_cheb_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, L.x.p, L.b.p, L.dinv.p, c,
+        KNP_SLOT_DISPATCH(L.A.slots, k_cheb_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, L.x.p, L.b.p, L.dinv.p, c,
                          L.d.p, L.x2.p);
     }
     std::swap(L.x.p, L.x2.p);
@@ -430,14 +439,14 @@ static void residual(DevLevel<T>& L, Profiler* pr, bool fine, cudaStream_t st) {
     if (L.sell) {
         k_resid_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, L.x.p, L.b.p, L.r.p);
     } else {
-        KNP_TPR_DISPATCH(L.A.tpr, k_resid_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, L.x.p, L.b.p, L.r.p);
+        KNP_SLOT_DISPATCH(L.A.slots, k_resid_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, L.x.p, L.b.p, L.r.p);
     }
 }
 
 template <class T>
 static void csr_apply(DevCsr4<T>& M, const T* x, T* y, int accumulate, cudaStream_t st) {
     count_launch();
-    KNP_TPR_DISPATCH(M.tpr, k_csr4, M.n, M.n, M.ptr.p, M.col.p, M.val.p, x, y, accumulate);
+    KNP_SLOT_DISPATCH(M.slots, k_csr4, M.n, M.n, M.ptr.p, M.col.p, M.val.p, x, y, accumulate);
 }
 
 template <class T>
@@ -620,7 +629,7 @@ static void na_cheb_step(DevLevel<T>& L, NaWork<T>& w, const Coef4& c, cudaStrea
         k_cheb_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, w.x, w.b, L.dinv.p, c, w.d,
                                                        w.x2);
     } else {
-        KNP_TPR_DISPATCH(L.A.tpr, k_cheb_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, w.x, w.b, L.dinv.p, c, w.d,
+        KNP_SLOT_DISPATCH(L.A.slots, k_cheb_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, w.x, w.b, L.dinv.p, c, w.d,
                          w.x2);
     }
     std::swap(w.x, w.x2);
@@ -652,13 +661,13 @@ static void na_vcycle_rec(AmgDev<T>& D, std::vector<NaWork<T>>& W, int l, const 
     if (L.sell) {
         k_resid_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, w.x, w.b, w.r);
     } else {
-        KNP_TPR_DISPATCH(L.A.tpr, k_resid_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, w.x, w.b, w.r);
+        KNP_SLOT_DISPATCH(L.A.slots, k_resid_csr, L.n, L.n, L.A.ptr.p, L.A.col.p, L.A.val.p, w.x, w.b, w.r);
     }
     count_launch();
-    KNP_TPR_DISPATCH(L.R.tpr, k_csr4, C.n, C.n, L.R.ptr.p, L.R.col.p, L.R.val.p, w.r, wc.b, 0);
+    KNP_SLOT_DISPATCH(L.R.slots, k_csr4, C.n, C.n, L.R.ptr.p, L.R.col.p, L.R.val.p, w.r, wc.b, 0);
     na_vcycle_rec(D, W, l + 1, nullptr, nullptr, st);
     count_launch();
-    KNP_TPR_DISPATCH(L.P.tpr, k_csr4, L.n, L.n, L.P.ptr.p, L.P.col.p, L.P.val.p, wc.x, w.x, 1);
+    KNP_SLOT_DISPATCH(L.P.slots, k_csr4, L.n, L.n, L.P.ptr.p, L.P.col.p, L.P.val.p, wc.x, w.x, 1);
     for (int k = 0; k < D.degree; ++k) na_cheb_step(L, w, cs[k], st);
 }
 
