@@ -179,8 +179,8 @@ def kernel_source_hash():
     k_cheb_sell), so that DRAM counters taken on an older version of it are not reported."""
     src = open(os.path.join(ROOT, "paper_2403_04491_gb300", "csrc", "vcycle.cu")).read()
     parts = []
-    for start, end in (("// Row product of a sliced-ELL operator", "// Row product of a CSR operator"),
-                       ("// Chebyshev update of one row", "template <class T, int TPR>\n__global__ void __launch_bounds__(128) k_cheb_csr")):
+    for start, end in (("// Row product of a sliced-ELL operator", "// Field f of a CSR row product"),
+                       ("// Chebyshev update of one row", "template <class T, int S>\n__global__ void __launch_bounds__(128) k_cheb_csr")):
         i = src.index(start)
         parts.append(src[i:src.index(end, i)])
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]

@@ -16,10 +16,11 @@
 // alone is blind to the per-cell constant of phi_i (the intracellular potential block is
 // singular up to the small membrane mass), while M^-1 r approximates the error. For the
 // FGMRES iterate, M^-1 r_k = Z_{k+1} c with c = Q_k^T g_k e_{k+1} from the Givens rotations,
-// so its S-norms follow from the S^2-weighted Gram matrices of Z, one row per iteration
-// (and so do those of the correction Z y_k).
+// so its group S-norms (and those of the correction Z y_k) take one pass over Z. That pass is
+// made only when the test may pass: each evaluation records est_g / |g_k|, and the next is
+// scheduled once that ratio times the current Givens residual |g_k| comes near the threshold.
 // (Apart, because the scaled concentrations outweigh the scaled potentials by two orders.)
-// The host sees one Hessenberg column and one Gram row per iteration.
+// The host sees one Hessenberg column per iteration.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -37,6 +38,12 @@ constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int MAXV = 32;          // restart + 2
 constexpr int MAXW = 3 * MAXV;    // partial-sum slots per block
+// device scalars: [0, MAXV) first-pass dots, [MAXV, 2 MAXV) second-pass dots, [2 MAXV, 2 MAXV +
+// MAXW) reference norms, 2 MAXV + MAXW the skip flag, then the six stopping-test norms
+constexpr int CHK_OFF = 2 * MAXV + MAXW + 1;
+constexpr int DOTS_LEN = CHK_OFF + 6;
+constexpr int CHECK_EVERY = 8;        // steps between exact evaluations of the stopping test, at most
+constexpr double CHECK_MARGIN = 4.0;  // evaluate once a prediction is within this factor of passing
 
 // Every kernel below is instantiated for a compile-time vector count NV, so that the
 // accumulators and basis values stay in registers (a runtime count put them on the stack).
@@ -139,6 +146,47 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_split(int64_t n4, const do
     block_reduce_store<NG * (NV + 1)>(out, partial);
 }
 
+// S^2-weighted squared norms, by group, of two combinations of the columns of Z:
+// u = sum_k c[k] Z_k and v = sum_k y[k] Z_k (y[NV-1] is the newest column's, often 0).
+// Slot g holds group g's part of ||u||_S^2 and slot NG + g that of ||v||_S^2 (groups as above).
+template <int NV, int NG>
+__global__ void __launch_bounds__(RED_THREADS) k_combo_norms(int64_t n4, const double* __restrict__ Z, int64_t ldz,
+                                                             const double* __restrict__ cy, const double* __restrict__ s,
+                                                             int64_t n4i, double* __restrict__ partial) {
+    double ck[NV > 0 ? NV : 1], yk[NV > 0 ? NV : 1];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        ck[k] = cy[k];
+        yk[k] = cy[MAXV + k];
+    }
+    double out[2 * NG];
+#pragma unroll
+    for (int k = 0; k < 2 * NG; ++k) out[k] = 0.0;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool phi = (i0 & 3) == 3;   // the grid stride is a multiple of 4
+    for (int64_t i = i0; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        double u = 0.0, v = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double zk = Z[k * ldz + i];
+            u += ck[k] * zk;
+            v += yk[k] * zk;
+        }
+        const double w = s[i];
+        u *= w;
+        v *= w;
+        const int grp = phi ? ((NG == 3 && i >= n4i) ? 2 : 1) : 0;
+#pragma unroll
+        for (int q = 0; q < NG; ++q) {
+            if (grp == q) {
+                out[q] += u * u;
+                out[NG + q] += v * v;
+            }
+        }
+    }
+    block_reduce_store<2 * NG>(out, partial);
+}
+
 // w' = w - sum_k h[k] V_k (in place); partial sums of <V_k, w'> and <w', w'>
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS) k_orth_update_dot(int64_t n4, const double* __restrict__ V, int64_t ldv,
@@ -233,6 +281,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_x(int64_t n4, const doub
 #define KNP_NV_CASE_k_mdot(N) case N: k_mdot<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
 #define KNP_NV_CASE_k_mdot_split2(N) case N: k_mdot_split<N, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
 #define KNP_NV_CASE_k_mdot_split3(N) case N: k_mdot_split<N, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_combo_norms2(N) case N: k_combo_norms<N, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_combo_norms3(N) case N: k_combo_norms<N, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
 #define KNP_NV_CASE_k_orth_update_dot(N) \
     case N: k_orth_update_dot<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
 #define KNP_NV_CASE_k_orth_final(N) case N: k_orth_final<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
@@ -262,7 +312,7 @@ __global__ void k_scale_inplace(int64_t n4, double* __restrict__ v, double s) {
 struct GmresWork {
     int restart = 0;
     int64_t n4 = 0;
-    DArray<double> V, Z, partial, dots, y, tmp;
+    DArray<double> V, Z, partial, dots, y, cy, tmp;
     std::vector<double> hh;
 };
 
@@ -276,10 +326,11 @@ GmresWork* gmres_work(knp_problem* p, int restart) {
     g->V.alloc((restart + 1) * g->n4);
     g->Z.alloc((restart + 1) * g->n4);
     g->partial.alloc(RED_BLOCKS * MAXW);
-    g->dots.alloc(2 * MAXV + MAXW + 1);
+    g->dots.alloc(DOTS_LEN);
     g->y.alloc(MAXV);
+    g->cy.alloc(2 * MAXV);
     g->tmp.alloc(g->n4);
-    g->hh.resize(2 * MAXV + MAXW + 1);
+    g->hh.resize(DOTS_LEN);
     p->gw = g;
     return g;
 }
@@ -337,8 +388,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     knp_status_detail res{KNP_OK, 0, 0, 0.0};
     // KNP_GMRES_MONITOR set: every iteration prints the stopping test's terms to stderr
     static const bool monitor = std::getenv("KNP_GMRES_MONITOR") != nullptr;
-    const int m1 = m + 1;
-    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), G(NG * m1 * m1);
+    std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), cyh(2 * MAXV);
     int its = 0, restarts = 0;
     bool converged = false;
     double beta = 0;
@@ -359,20 +409,55 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
         int k_done = 0;   // Arnoldi steps whose Hessenberg columns are kept
+        // The stopping test is evaluated exactly (one pass over Z) at the first step of a cycle,
+        // at its last, at least every CHECK_EVERY steps, and whenever the group norms predicted
+        // from the last evaluation (est_g scaled by the Givens residual |g_j|) come within
+        // CHECK_MARGIN of their thresholds; convergence is only ever declared from an evaluation.
+        double ratio[3] = {0, 0, 0}, corr_last[3] = {0, 0, 0};
+        int last_check = -1;
         for (int j = 0; j <= m; ++j) {
             double* vj = g.V.p + (int64_t)j * n4;
             double* zj = g.Z.p + (int64_t)j * n4;
-            // z_j = V-cycle(S v_j); row j of the S^2-weighted Gram matrices of Z (two field groups)
+            // z_j = V-cycle(S v_j)
             vcycle_apply(p, vj, p->svec.p, zj);
-            count_launch(2);
-#define KNP_ARGS n4, g.Z.p, n4, zj, p->swt.p, n4i, g.partial.p
-            if (NG == 3)
-                KNP_LAUNCH_NV(j, k_mdot_split3);
-            else
-                KNP_LAUNCH_NV(j, k_mdot_split2);
-#undef KNP_ARGS
-            k_reduce<<<NG * (j + 1), 256, 0, st>>>(g.partial.p, RED_BLOCKS, NG * (j + 1), g.dots.p + 2 * MAXV);
             const bool arnoldi = (j < m) && (its < o.max_it);
+            bool check = last_check < 0 || !arnoldi || j - last_check >= CHECK_EVERY;
+            if (!check) {
+                check = true;
+                for (int q = 0; q < NG; ++q) {
+                    const double ref = std::max(tol[q], o.rtol * corr_last[q]);
+                    if (ratio[q] * std::fabs(gv[j]) > CHECK_MARGIN * ref) check = false;
+                }
+            }
+            if (check) {
+                // preconditioned residual of the iterate after j steps: M^-1 r = Z c with
+                // c = Q^T (0, .., 0, g_j); the correction of this cycle, x_j - x_c = Z y_j
+                const int k = j;
+                std::fill(cyh.begin(), cyh.end(), 0.0);
+                double* c = cyh.data();
+                double* yk = cyh.data() + MAXV;
+                c[k] = gv[k];
+                for (int i = k - 1; i >= 0; --i) {
+                    double a = c[i], b = c[i + 1];
+                    c[i] = cs[i] * a - sn[i] * b;
+                    c[i + 1] = sn[i] * a + cs[i] * b;
+                }
+                for (int i = k - 1; i >= 0; --i) {
+                    double sacc = gv[i];
+                    for (int q2 = i + 1; q2 < k; ++q2) sacc -= H[i * m + q2] * yk[q2];
+                    yk[i] = sacc / H[i * m + i];
+                }
+                KNP_CUDA(cudaMemcpyAsync(g.cy.p, cyh.data(), 2 * MAXV * sizeof(double), cudaMemcpyHostToDevice,
+                                         st));
+                count_launch(2);
+#define KNP_ARGS n4, g.Z.p, n4, g.cy.p, p->swt.p, n4i, g.partial.p
+                if (NG == 3)
+                    KNP_LAUNCH_NV(j + 1, k_combo_norms3);
+                else
+                    KNP_LAUNCH_NV(j + 1, k_combo_norms2);
+#undef KNP_ARGS
+                k_reduce<<<2 * NG, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2 * NG, g.dots.p + CHK_OFF);
+            }
             int nv = j + 1;
             if (arnoldi) {
                 double* w = g.V.p + (int64_t)(j + 1) * n4;
@@ -391,48 +476,25 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                 KNP_LAUNCH_NV(nv, k_orth_final);
 #undef KNP_ARGS
             }
-            KNP_CUDA(cudaMemcpyAsync(g.hh.data(), g.dots.p, (2 * MAXV + MAXW + 1) * sizeof(double),
-                                     cudaMemcpyDeviceToHost, st));
+            KNP_CUDA(cudaMemcpyAsync(g.hh.data(), g.dots.p, DOTS_LEN * sizeof(double), cudaMemcpyDeviceToHost, st));
             KNP_CUDA(cudaStreamSynchronize(st));
             KNP_CUDA(cudaGetLastError());
-            for (int q = 0; q < NG; ++q)
-                for (int a = 0; a <= j; ++a)
-                    G[q * m1 * m1 + j * m1 + a] = G[q * m1 * m1 + a * m1 + j] = g.hh[2 * MAXV + NG * a + q];
-
-            // preconditioned residual of the iterate after k_done = j steps: M^-1 r = Z c with
-            // c = Q^T (0, .., 0, g_j); its S-norm is sqrt(c^T G c)
-            {
-                const int k = j;
-                std::vector<double> c(k + 1, 0.0);
-                c[k] = gv[k];
-                for (int i = k - 1; i >= 0; --i) {
-                    double a = c[i], b = c[i + 1];
-                    c[i] = cs[i] * a - sn[i] * b;
-                    c[i + 1] = sn[i] * a + cs[i] * b;
-                }
-                // the correction of this cycle, x_k - x_0 = Z y_k, and its S-norms y^T G y
-                std::vector<double> yk(k);
-                for (int i = k - 1; i >= 0; --i) {
-                    double sacc = gv[i];
-                    for (int q2 = i + 1; q2 < k; ++q2) sacc -= H[i * m + q2] * yk[q2];
-                    yk[i] = sacc / H[i * m + i];
-                }
+            if (check) {
                 bool ok = true;
-                if (monitor) std::fprintf(stderr, "fgmres%s it %d |g| %.3e", transpose ? "^T" : "", its, std::fabs(gv[k]));
+                if (monitor) std::fprintf(stderr, "fgmres%s it %d |g| %.3e", transpose ? "^T" : "", its, std::fabs(gv[j]));
                 for (int q = 0; q < NG; ++q) {
-                    double est2 = 0, corr2 = 0;
-                    for (int a = 0; a <= k; ++a)
-                        for (int b = 0; b <= k; ++b) est2 += c[a] * c[b] * G[q * m1 * m1 + a * m1 + b];
-                    for (int a = 0; a < k; ++a)
-                        for (int b = 0; b < k; ++b) corr2 += yk[a] * yk[b] * G[q * m1 * m1 + a * m1 + b];
-                    KNP_REQUIRE(std::isfinite(est2), KNP_ERR_NUMERIC, "preconditioned residual is not finite");
-                    const double ref = std::max(tol[q], o.rtol * std::sqrt(std::max(corr2, 0.0)));
-                    ok &= std::sqrt(std::max(est2, 0.0)) <= ref;
-                    if (monitor)
-                        std::fprintf(stderr, "  [%d] est %.3e (raw %.2e) tol %.3e corr %.3e", q,
-                                     std::sqrt(std::max(est2, 0.0)), est2, tol[q], std::sqrt(std::max(corr2, 0.0)));
+                    const double est2 = g.hh[CHK_OFF + q], corr2 = g.hh[CHK_OFF + NG + q];
+                    KNP_REQUIRE(std::isfinite(est2) && std::isfinite(corr2), KNP_ERR_NUMERIC,
+                                "preconditioned residual is not finite");
+                    const double est = std::sqrt(std::max(est2, 0.0)), corr = std::sqrt(std::max(corr2, 0.0));
+                    const double ref = std::max(tol[q], o.rtol * corr);
+                    ok &= est <= ref;
+                    ratio[q] = gv[j] != 0.0 ? est / std::fabs(gv[j]) : 0.0;
+                    corr_last[q] = corr;
+                    if (monitor) std::fprintf(stderr, "  [%d] est %.3e tol %.3e corr %.3e", q, est, tol[q], corr);
                 }
                 if (monitor) std::fprintf(stderr, "\n");
+                last_check = j;
                 if (ok) {
                     converged = true;
                     k_done = j;

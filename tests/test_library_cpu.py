@@ -97,3 +97,14 @@ def test_invalid_arguments_are_rejected(lib):
     with pytest.raises(KnpError) as ei:
         Mesh(flat, elems, np.zeros(len(elems), np.int32))
     assert ei.value.code == 2
+
+
+def test_bench_kernel_source_hash():
+    """bench.py locates the finest-level Chebyshev kernel's source text (the DRAM counters it
+    reports are tied to that text)."""
+    import importlib
+    import sys
+    sys.path.insert(0, str(ROOT))
+    bench = importlib.import_module("bench")
+    h = bench.kernel_source_hash()
+    assert isinstance(h, str) and len(h) == 16
