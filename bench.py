@@ -399,6 +399,9 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
     else:
         roof = dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=hbm["frac"],
                     peak_source=hbm["peak_source"], **common)
+    if mixed and args.precision == "fp64" and args.rtol == 1e-10:
+        # the mixed form at its tolerance (1e-8) against the plain FP64 path at its own (1e-10)
+        mixed["speedup_fp32_rtol_1e-08_vs_plain_fp64_rtol_1e-10"] = mixed["rtol_1e-08"]["value"] / value
     cpu = None
     if not args.no_baseline and world == 1 and args.config == 2:
         r = run_oracle(3, 1)

@@ -313,7 +313,12 @@ struct GmresWork {
     int restart = 0;
     int64_t n4 = 0;
     DArray<double> V, Z, partial, dots, y, cy, tmp;
-    std::vector<double> hh;
+    double* hh = nullptr;           // pinned copy of dots, DOTS_LEN
+    cudaEvent_t ev_dots = nullptr;  // recorded after the copy of dots to hh
+    ~GmresWork() {
+        if (hh) cudaFreeHost(hh);
+        if (ev_dots) cudaEventDestroy(ev_dots);
+    }
 };
 
 GmresWork* gmres_work(knp_problem* p, int restart) {
@@ -330,7 +335,8 @@ GmresWork* gmres_work(knp_problem* p, int restart) {
     g->y.alloc(MAXV);
     g->cy.alloc(2 * MAXV);
     g->tmp.alloc(g->n4);
-    g->hh.resize(DOTS_LEN);
+    KNP_CUDA(cudaMallocHost(&g->hh, DOTS_LEN * sizeof(double)));
+    KNP_CUDA(cudaEventCreateWithFlags(&g->ev_dots, cudaEventDisableTiming));
     p->gw = g;
     return g;
 }
@@ -415,11 +421,13 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         // CHECK_MARGIN of their thresholds; convergence is only ever declared from an evaluation.
         double ratio[3] = {0, 0, 0}, corr_last[3] = {0, 0, 0};
         int last_check = -1;
+        bool vc_queued = false;
         for (int j = 0; j <= m; ++j) {
             double* vj = g.V.p + (int64_t)j * n4;
             double* zj = g.Z.p + (int64_t)j * n4;
-            // z_j = V-cycle(S v_j)
-            vcycle_apply(p, vj, p->svec.p, zj);
+            // z_j = V-cycle(S v_j), unless the previous step queued it
+            if (!vc_queued) vcycle_apply(p, vj, p->svec.p, zj);
+            vc_queued = false;
             const bool arnoldi = (j < m) && (its < o.max_it);
             bool check = last_check < 0 || !arnoldi || j - last_check >= CHECK_EVERY;
             if (!check) {
@@ -476,8 +484,15 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                 KNP_LAUNCH_NV(nv, k_orth_final);
 #undef KNP_ARGS
             }
-            KNP_CUDA(cudaMemcpyAsync(g.hh.data(), g.dots.p, DOTS_LEN * sizeof(double), cudaMemcpyDeviceToHost, st));
-            KNP_CUDA(cudaStreamSynchronize(st));
+            KNP_CUDA(cudaMemcpyAsync(g.hh, g.dots.p, DOTS_LEN * sizeof(double), cudaMemcpyDeviceToHost, st));
+            KNP_CUDA(cudaEventRecord(g.ev_dots, st));
+            if (arnoldi) {
+                // v_{j+1} is already normalised on the device: queue its V-cycle before the host
+                // waits for this step's dots, so the GPU works while the host does the Givens step
+                vcycle_apply(p, g.V.p + (int64_t)(j + 1) * n4, p->svec.p, g.Z.p + (int64_t)(j + 1) * n4);
+                vc_queued = true;
+            }
+            KNP_CUDA(cudaEventSynchronize(g.ev_dots));
             KNP_CUDA(cudaGetLastError());
             if (check) {
                 bool ok = true;

@@ -295,8 +295,6 @@ struct AmgDev {
 AmgHierarchy::~AmgHierarchy() {
     for (auto& kv : graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    if (ev_in) cudaEventDestroy(ev_in);
-    if (ev_out) cudaEventDestroy(ev_out);
     if (gstream) cudaStreamDestroy(gstream);
     delete static_cast<AmgDev<double>*>(h64);
     delete static_cast<AmgDev<float>*>(h32);
@@ -499,8 +497,9 @@ static void vcycle_launch(knp_problem* p, const double* v, const double* s, doub
 }
 
 // z = V-cycle(P_0)(s .* v); v, s, z are [n][4] doubles on the device. The V-cycle is a fixed
-// sequence of about 25 launches, so it is captured once per (v, s, z) into a CUDA graph and
-// replayed on a private stream ordered after the caller's stream. Each replay starts from
+// sequence of about 15 launches, so it is captured once per (v, s, z) into a CUDA graph (on a
+// private stream, since the problem's stream may be the legacy one) and replayed on the
+// problem's stream. Each replay starts from
 // scratch (the first kernel writes b, x and d of the finest level), so replays are independent.
 // While a kernel class is being profiled the launches go out one by one.
 void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
@@ -515,8 +514,6 @@ void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
     }
     if (!H.gstream) {
         KNP_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
-        KNP_CUDA(cudaEventCreateWithFlags(&H.ev_in, cudaEventDisableTiming));
-        KNP_CUDA(cudaEventCreateWithFlags(&H.ev_out, cudaEventDisableTiming));
     }
     auto key = std::make_tuple(v, s, z);
     auto it = H.graphs.find(key);
@@ -540,11 +537,7 @@ void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
         cudaGraphDestroy(graph);
         it = H.graphs.emplace(key, g).first;
     }
-    KNP_CUDA(cudaEventRecord(H.ev_in, st));
-    KNP_CUDA(cudaStreamWaitEvent(H.gstream, H.ev_in, 0));
-    KNP_CUDA(cudaGraphLaunch(it->second.exec, H.gstream));
-    KNP_CUDA(cudaEventRecord(H.ev_out, H.gstream));
-    KNP_CUDA(cudaStreamWaitEvent(st, H.ev_out, 0));
+    KNP_CUDA(cudaGraphLaunch(it->second.exec, st));
     count_launch(it->second.launches);
 }
 

@@ -21,10 +21,9 @@ struct AmgHierarchy {
     std::vector<int64_t> nodes, nnz;
     void* h64 = nullptr;   // AmgDev<double>
     void* h32 = nullptr;   // AmgDev<float>
-    // CUDA graphs of the V-cycle (one per FGMRES basis slot), replayed on a private stream
+    // CUDA graphs of the V-cycle (one per FGMRES basis slot), captured on a private stream
     bool use_graphs = true;
     cudaStream_t gstream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::map<std::tuple<const double*, const double*, double*>, VcycleGraph> graphs;
     ~AmgHierarchy();
 };
