@@ -380,7 +380,8 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
     if os.path.exists(PROFILE_FILE):
         pf = json.load(open(PROFILE_FILE))
         ent = pf.get(f"cheb_fine_{args.precision}")
-        if ent and ent.get("source_hash") == kernel_source_hash():
+        # counters hold for the kernel text and the workload they were taken on
+        if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("n_dof") == n_dof:
             traffic = ent.get("dram_bytes_per_launch")
     hbm = dict(achieved=gbs, peak=peak, unit="GB/s", frac=(gbs / peak) if gbs else None,
                peak_source="measured" if "hbm_gbs" in peaks else "fallback")

@@ -42,8 +42,8 @@ constexpr int MAXW = 3 * MAXV;    // partial-sum slots per block
 // MAXW) reference norms, 2 MAXV + MAXW the skip flag, then the six stopping-test norms
 constexpr int CHK_OFF = 2 * MAXV + MAXW + 1;
 constexpr int DOTS_LEN = CHK_OFF + 6;
-constexpr int CHECK_EVERY = 8;        // steps between exact evaluations of the stopping test, at most
-constexpr double CHECK_MARGIN = 4.0;  // evaluate once a prediction is within this factor of passing
+constexpr int CHECK_EVERY = 4;         // steps between exact evaluations of the stopping test, at most
+constexpr double CHECK_MARGIN = 10.0;  // evaluate once a prediction is within this factor of passing
 
 // Every kernel below is instantiated for a compile-time vector count NV, so that the
 // accumulators and basis values stay in registers (a runtime count put them on the stack).
