@@ -234,6 +234,23 @@ def measure(prob, torch, steps, rtol, kernel_class=None):
     return e0.elapsed_time(e1), iters, launches, prof
 
 
+def slowest_rank_ms(ms, world, device):
+    """Whole-job time of N replicas: the ranks meet at a barrier and take the largest time."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_dof, steps, world, ms):
+    """DOF x steps of all replicas per second of the slowest rank's time."""
+    return n_dof * steps * world / (ms / 1e3)
+
+
 def ours(args):
     import numpy as np
     import torch
@@ -281,12 +298,7 @@ def ours(args):
     # same number of steps (event pairs go around single launches, so the V-cycle is not replayed
     # from its CUDA graph in this pass)
     _, _, _, prof = measure(prob, torch, args.steps, args.rtol, kernel_class=1)
-    if world > 1:
-        dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_dof * args.steps * world / (ms / 1e3)
+    ms = slowest_rank_ms(ms, world, "cuda")
 
     # end to end through the public API with host buffers: per step the state goes host->device,
     # one knp_step runs, and the new state comes back device->host (pinned host memory)
@@ -325,11 +337,8 @@ def e2e_run(prob, torch, args, n_dof, world):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = n_dof * args.steps * world / (e2e_ms / 1e3)
+    e2e_ms = slowest_rank_ms(e2e_ms, world, "cuda")
+    e2e_value = job_value(n_dof, args.steps, world, e2e_ms)
     return dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=h2d)
 
 
@@ -364,7 +373,7 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
            workload=WORKLOAD, mem_gb=None):
     import numpy as np
     import torch.distributed as dist
-    value = n_dof * args.steps * world / (ms / 1e3)
+    value = job_value(n_dof, args.steps, world, ms)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

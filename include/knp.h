@@ -144,11 +144,12 @@ knp_status knp_assemble_step(knp_problem* prob);
 typedef struct {
     int32_t precision;          /* knp_precision of the hierarchy and V-cycle (FGMRES stays FP64) */
     double theta;               /* strength threshold of the aggregation graph (0.08 default) */
-    int32_t coarse_max;         /* stop coarsening at <= this many nodes (dense coarse solve) */
-    int32_t max_levels;
-    int32_t cheb_degree;        /* Chebyshev smoothing degree (pre and post) */
-    double cheb_ratio;          /* lower eigenvalue bound = lambda_max / cheb_ratio */
-    double theta_coarse;        /* strength threshold on levels >= 1 (< 0: same as theta) */
+    int32_t coarse_max;         /* stop coarsening at <= this many nodes (dense coarse solve; 500) */
+    int32_t max_levels;         /* (12) */
+    int32_t cheb_degree;        /* Chebyshev smoothing degree, pre and post (1; 2 gives the same
+                                   iteration counts on the 3D workloads at twice the smoothing cost) */
+    double cheb_ratio;          /* lower eigenvalue bound = lambda_max / cheb_ratio (4) */
+    double theta_coarse;        /* strength threshold on levels >= 1 (< 0: same as theta; 0) */
     double p_drop;              /* drop prolongator entries below p_drop x the row's largest (0: keep all) */
     int32_t host_setup;         /* 1: build the hierarchy on the host (reference path); 0: on the GPU */
 } knp_amg_opts;

@@ -51,3 +51,10 @@ def blockwise_vector_error(pb, y, yr):
         den = np.abs(yr[a:c]).max()
         errs.append(np.abs(y[a:c] - yr[a:c]).max() / den if den > 0 else np.abs(y[a:c]).max())
     return float(max(errs))
+
+
+def paper_values():
+    """Values printed in the paper, with their citations (tests/golden/paper_values.json)."""
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))

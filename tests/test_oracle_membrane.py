@@ -6,13 +6,16 @@ import pytest
 from oracle import membrane
 from synth.configs import table2
 
+from helpers import paper_values
+
 
 def test_gates_at_phi_M0_match_table2():
     p = table2()
     V = 1e3 * (p["phi_M0"] - p["phi_rest"])           # -2.74 mV
     n, m, h = membrane.hh_steady_state(np.array([V]))[:, 0]
     # Table 2: n0 = 0.276, m0 = 0.0379, h0 = 0.688 (printed to 3 significant digits)
-    assert abs(n - p["n0"]) < 1.5e-3 and abs(m - p["m0"]) < 5e-4 and abs(h - p["h0"]) < 1.5e-3
+    g = paper_values()["table2_initial_gates"]
+    assert abs(n - g["n0"]) < 1.5e-3 and abs(m - g["m0"]) < 5e-4 and abs(h - g["h0"]) < 1.5e-3
 
 
 def test_textbook_resting_values():

@@ -11,6 +11,8 @@ from oracle import fem, problem, solve, step, system
 from synth import make_config
 from synth.configs import MODEL_LEAK, model_a
 
+from helpers import paper_values
+
 
 def _steady_problem(d, nx):
     cfg = model_a(d, nx, 1e-4)
@@ -98,7 +100,9 @@ def test_lu_P0_gmres_iteration_counts_section_6_3(nx):
     """Section 6.3: one step of 2D Model A, LU(P_0)-GMRES, preconditioned relative residual 1e-6:
     4 iterations for dt in {0.01, 0.1} ms and 3 for dt in {10, 100} ms (3 printed for 1 ms; this
     reading needs 4 there, its third iterate stops at 1.9e-6, just above the tolerance)."""
-    expect = {1e-5: 4, 1e-4: 4, 1e-3: (3, 4), 1e-2: 3, 1e-1: 3}
+    printed = paper_values()["section6_3_lu_p0_iterations"]
+    expect = dict(zip(printed["dt_s"], printed["iterations"]))
+    expect[1e-3] = (3, 4)   # the reading noted above
     for dt, n_exp in expect.items():
         pb, s0 = problem.from_config(model_a(2, nx, dt))
         A, f, _ = system.assemble(pb, s0)
