@@ -9,6 +9,10 @@ integrals as P1 functions.
 * C_r^k = alpha_r^k C_m / (F z_k)                                            (Eq. 3.6)
 * Hodgkin-Huxley gates by N_ode Rush-Larsen substeps with phi_M frozen at phi_M^{n-1} (Section 3.2)
 * channel driving terms q = G(w) (phi_M - E_k): leak G = 1, HH Na m^3 h, HH K n^4 (Eq. 2.15)
+* Kir-Na/K (Section 2.4.2): the K leak is rectified by f_Kir([K]_e, phi_M - E_K, phi_M), and a
+  Na/K pump of flux density j_pump([Na]_i, [K]_e) adds 3 F z_Na j_pump to the Na current and
+  -2 F z_K j_pump to the K current. E_K^0 and [K]_e^0 are the t = 0 values (the uniform
+  initial concentrations).
 
 The HH-1952 rates are not printed in the paper (Section 2.4.1 cites HH-1952);
 the reading used is the textbook set in the modern sign convention with
@@ -83,3 +87,21 @@ def stimulus_conductance(kind, gbar, t, t0, t1, a, tau):
     if kind == 2:
         return gbar * np.exp(-np.mod(t, tau) / a)
     raise ValueError(kind)
+
+
+def kir_factor(cKe, dphi_K, phi_M, E_K0, cKe0):
+    """f_Kir of Section 2.4.2 (potentials in volts, concentrations in mol/m^3):
+    A B / (C D) sqrt([K]_e / [K]_e^0) with A = 1 + e^0.433, B = 1 + e^{-(0.1186 + E_K^0)/0.0441},
+    C = 1 + e^{(dphi_K + 0.0185)/0.0425}, D = 1 + e^{-(0.1186 + phi_M)/0.0441}, dphi_K = phi_M - E_K."""
+    A = 1.0 + np.exp(0.433)
+    B = 1.0 + np.exp(-(0.1186 + E_K0) / 0.0441)
+    C = 1.0 + np.exp((dphi_K + 0.0185) / 0.0425)
+    D = 1.0 + np.exp(-(0.1186 + phi_M) / 0.0441)
+    return A * B / (C * D) * np.sqrt(cKe / cKe0)
+
+
+def pump_flux(cNa_i, cK_e, rho, P_Na, P_K):
+    """Na/K pump flux density (mol/(m^2 s)) of Section 2.4.2:
+    rho [Na]_i^1.5 / ([Na]_i^1.5 + P_Na^1.5) * [K]_e / ([K]_e + P_K)."""
+    a = cNa_i ** 1.5
+    return rho * a / (a + P_Na ** 1.5) * cK_e / (cK_e + P_K)

@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import system
+from . import membrane, system
 from .topology import build_topology
 
 
@@ -32,7 +32,14 @@ def from_config(cfg, dt=None):
                         gbar_K=p["gbar_K"], phi_rest=p["phi_rest"], n_ode=25,
                         stim_kind=cfg.stim_kind, stim_gbar=cfg.stim_gbar, stim_t0=cfg.stim_t0,
                         stim_t1=cfg.stim_t1, stim_a=cfg.stim_a, stim_tau=cfg.stim_tau,
-                        stim_mask=mask)
+                        stim_mask=mask, rho_pump=p["rho_pump"], P_Na=p["P_Na"], P_K=p["P_K"],
+                        cKe0=p["c_e0"][1])
+    # E_K^0 of the Kir factor: the K reversal potential of the initial concentrations
+    pb.E_K0 = float(membrane.reversal_potential(p["R"], p["T"], p["F"], p["z"][1], p["c_i0"][1], p["c_e0"][1]))
+    src = cfg.vertex_source_e()
+    if src is not None:
+        pb.source_e = np.ascontiguousarray(src[topo.nodes_e].T)
+        pb.source_t0, pb.source_t1 = cfg.source_t0, cfg.source_t1
     system.discretize(pb)
     s0 = system.initial_state(pb, p["c_i0"], p["c_e0"], p["phi_M0"], (p["n0"], p["m0"], p["h0"]))
     return pb, s0

@@ -5,7 +5,10 @@ block in region node order. Blocks follow the matrices A_r^n and B_rq^n of
 Section 4.1 with tau_r^k = dt D_r^k and tau~_r^k = tau_r^k z_k / psi, psi = RT/F.
 
 Readings where the paper is silent or inconsistent (also listed in the design doc):
-  * the bulk source enters the right-hand side multiplied by dt (Eq. 3.5 omits it);
+  * the bulk source enters the right-hand side multiplied by dt (Eq. 3.5 omits it), with
+    nodal values, evaluated at t_n (f_r^{k,n} of Section 3.2);
+  * Kir-Na/K facets (Section 2.4.2): the rectification factor and the pump flux are nodal, like
+    every other membrane coefficient; E_K^0 and [K]_e^0 are the initial (uniform) values;
   * h_r = +-_r (dt I_ch - C_m phi_M^{n-1}) / F: the printed "+C_m phi_M" contradicts a
     re-derivation of h_r in Eq. 3.7 from Eq. 3.2 with the backward difference of Section 3.2;
   * alpha and C are nodal P1 on Gamma; int_Gamma C phi_M v is the exact triple product,
@@ -29,7 +32,7 @@ import scipy.sparse as sp
 from . import fem, membrane
 from .topology import Topology, build_topology
 
-LEAK, HH = 0, 1
+LEAK, HH, KIR = 0, 1, 2
 
 
 @dataclass
@@ -58,6 +61,18 @@ class Problem:
     stim_a: float = 2e-3
     stim_tau: float = 10e-3
     stim_mask: np.ndarray = None       # (n_f,) bool
+    # Kir-Na/K (Section 2.4.2): pump constants, E_K^0 and [K]_e^0 (t = 0 values)
+    rho_pump: float = 1.115e-6
+    P_Na: float = 10.0
+    P_K: float = 1.5
+    E_K0: float = 0.0
+    cKe0: float = 4.0
+    # bulk source f_r^k(x, t_n) (mol/(m^3 s)): nodal values per region, (n_ions, N_r), switched on
+    # for source_t0 < t_n <= source_t1; None = no source
+    source_i: np.ndarray = None
+    source_e: np.ndarray = None
+    source_t0: float = 0.0
+    source_t1: float = 0.0
     geo: dict = field(default_factory=dict)
 
     @property
@@ -164,7 +179,7 @@ def membrane_fields(pb: Problem, s: State):
     C_i = a_i * pb.Cm / (pb.F * z[:, None])
     C_e = a_e * pb.Cm / (pb.F * z[:, None])
     w_new = membrane.rush_larsen(s.w, phi_M, pb.phi_rest, pb.dt, pb.n_ode)
-    return dict(phi_M=phi_M, E=E, a_i=a_i, a_e=a_e, C_i=C_i, C_e=C_e, w=w_new)
+    return dict(phi_M=phi_M, E=E, a_i=a_i, a_e=a_e, C_i=C_i, C_e=C_e, w=w_new, c_i=ci, c_e=ce)
 
 
 def channel_currents(pb: Problem, mf: dict, t_prev: float) -> np.ndarray:
@@ -180,6 +195,7 @@ def channel_currents(pb: Problem, mf: dict, t_prev: float) -> np.ndarray:
     gstim = membrane.stimulus_conductance(pb.stim_kind, pb.stim_gbar, t_prev, pb.stim_t0,
                                           pb.stim_t1, pb.stim_a, pb.stim_tau)
     hh = (pb.facet_model == HH).astype(float)
+    kir = pb.facet_model == KIR
     I = np.empty((pb.n_ions,) + fv.shape)
     for k in range(pb.n_ions):
         I[k] = pb.facet_gleak[:, k][:, None] * drive[k][fv]
@@ -187,6 +203,13 @@ def channel_currents(pb: Problem, mf: dict, t_prev: float) -> np.ndarray:
     I[0] += (gstim * pb.stim_mask)[:, None] * drive[0][fv]
     I[0] += (hh * pb.gbar_Na)[:, None] * (m_g ** 3 * h_g * drive[0])[fv]
     I[1] += (hh * pb.gbar_K)[:, None] * (n_g ** 4 * drive[1])[fv]
+    if kir.any():
+        # Kir-Na/K: K leak g_leak^K (phi_M - E_K) f_Kir, pump 3 F z_Na j and -2 F z_K j
+        f_kir = membrane.kir_factor(mf["c_e"][1], drive[1], phi_M, pb.E_K0, pb.cKe0)
+        j = membrane.pump_flux(mf["c_i"][0], mf["c_e"][1], pb.rho_pump, pb.P_Na, pb.P_K)
+        I[1][kir] = pb.facet_gleak[kir, 1][:, None] * (drive[1] * f_kir)[fv[kir]]
+        I[0][kir] += 3.0 * pb.F * pb.z[0] * j[fv[kir]]
+        I[1][kir] -= 2.0 * pb.F * pb.z[1] * j[fv[kir]]
     return I
 
 
@@ -200,6 +223,11 @@ def assemble(pb: Problem, s: State, source=None):
     mf = membrane_fields(pb, s)
     I = channel_currents(pb, mf, s.t)
     fv, area = g["fv"], g["area"]
+    if source is None and (pb.source_i is not None or pb.source_e is not None):
+        # the problem's own bulk source, evaluated at t_n = t_{n-1} + dt
+        if pb.source_t0 < s.t + dt <= pb.source_t1:
+            source = {"i": pb.source_i if pb.source_i is not None else np.zeros((K, Ni)),
+                      "e": pb.source_e if pb.source_e is not None else np.zeros((K, Ne))}
     blocks = [[None] * (2 * (K + 1)) for _ in range(2 * (K + 1))]
     rhs = []
     regions = (("i", "e", +1.0, s.c_i, pb.D_i, mf["a_i"], mf["C_i"], g["fi"], g["fe"], Ni, Ne, 0),

@@ -32,7 +32,7 @@ def table2() -> dict:
 # stimulus kinds
 STIM_NONE, STIM_WINDOW, STIM_PERIODIC_EXP = 0, 1, 2
 # membrane models
-MODEL_LEAK, MODEL_HH = 0, 1
+MODEL_LEAK, MODEL_HH, MODEL_KIR = 0, 1, 2
 
 
 @dataclass
@@ -43,7 +43,7 @@ class Config:
     length: float                 # metres
     cell_lo: np.ndarray           # (n_cells, dim) fractions of the side
     cell_hi: np.ndarray
-    model: int                    # MODEL_LEAK or MODEL_HH (all facets)
+    model: int                    # MODEL_LEAK, MODEL_HH or MODEL_KIR (all facets)
     g_leak: tuple                 # (Na, K, Cl) S/m^2
     dt: float                     # s
     n_steps: int
@@ -58,6 +58,10 @@ class Config:
     stim_xmax: float = np.inf     # stimulated facets: centroid x < stim_xmax (metres)
     gK_sigma: float = 0.0         # per-facet g_K = g_leak_K * exp(sigma * xi)
     seed_gK: int = 1
+    source_e: Optional[tuple] = None  # bulk source (Na, K, Cl), mol/(m^3 s), on extracellular
+    source_xmax: float = np.inf       # vertices with x < source_xmax (metres), switched on
+    source_t0: float = 0.0            # for source_t0 < t_n <= source_t1
+    source_t1: float = 0.0
     params: dict = field(default_factory=table2)
     _mesh: Optional[StructuredMesh] = None
 
@@ -77,6 +81,15 @@ class Config:
         rng = np.random.Generator(np.random.PCG64(self.seed_gK))
         return rng.standard_normal((m.elems.shape[0], self.dim + 1))
 
+    def vertex_source_e(self) -> Optional[np.ndarray]:
+        """(n_vertices, n_ions) bulk source values for the extracellular copy of each vertex:
+        source_e where the vertex's x < source_xmax, else 0; None without a source."""
+        if self.source_e is None:
+            return None
+        m = self.mesh
+        on = (m.coords[:, 0] < self.source_xmax).astype(float)
+        return on[:, None] * np.asarray(self.source_e, float)[None, :]
+
     def with_nx(self, nx: int) -> "Config":
         return replace(self, nx=nx, _mesh=None)
 
@@ -86,7 +99,7 @@ def _single(dim, lo, hi):
 
 
 def make_config(i: int) -> Config:
-    """Configs 1..5: the synthetic workloads (see the design doc for the recipe)."""
+    """Configs 1..5: the synthetic workloads; 6, 7: the Kir-Na/K workloads with a bulk source."""
     L = 100e-6
     if i == 1:
         lo, hi = _single(2, 0.25, 0.75)
@@ -112,6 +125,18 @@ def make_config(i: int) -> Config:
         return Config("cfg5-3d-256-512cells-mixed", 3, 256, L, lo, hi, MODEL_HH, (0.2, 0.8, 0.0),
                       dt=5e-5, n_steps=50, rtol=1e-8, mixed=True, stim_kind=STIM_WINDOW,
                       stim_gbar=40.0, stim_t0=0.0, stim_t1=1e-3, stim_xmax=0.4 * L)
+    if i == 6:
+        # Kir-Na/K membrane with a K bolus and Na removal in the extracellular half x < L/2 for
+        # 0 < t <= 2 ms (Section 5.2's stimulus on a Model-A-shaped box; Table 2 leak values)
+        lo, hi = _single(3, 0.3, 0.7)
+        return Config("kir-3d-64-bolus", 3, 64, L, lo, hi, MODEL_KIR, (1.0, 4.0, 0.0),
+                      dt=1e-4, n_steps=50, rtol=1e-10, source_e=(-1.0, 1.0, 0.0), source_xmax=0.5 * L,
+                      source_t0=0.0, source_t1=2e-3)
+    if i == 7:
+        lo, hi = _single(2, 0.25, 0.75)
+        return Config("kir-2d-32-bolus", 2, 32, L, lo, hi, MODEL_KIR, (1.0, 4.0, 0.0),
+                      dt=1e-4, n_steps=30, rtol=1e-10, source_e=(-1.0, 1.0, 0.0), source_xmax=0.5 * L,
+                      source_t0=0.0, source_t1=2e-3)
     raise ValueError(i)
 
 
@@ -125,7 +150,7 @@ def model_a(dim: int, nx: int, dt: float) -> Config:
                   stim_a=p["stim_a"], stim_tau=p["stim_tau"])
 
 
-CONFIGS = {i: (lambda i=i: make_config(i)) for i in range(1, 6)}
+CONFIGS = {i: (lambda i=i: make_config(i)) for i in range(1, 8)}
 
 
 def probe_points(cfg: Config, n: int = 64, seed: int = 2) -> np.ndarray:

@@ -71,3 +71,45 @@ def test_stimulus_shapes():
     assert membrane.stimulus_conductance(1, 40.0, 1e-3, 0.0, 1e-3, 0, 0) == 0.0
     g = membrane.stimulus_conductance(2, 40.0, 12e-3, 0, 0, 2e-3, 10e-3)
     assert abs(g - 40.0 * np.exp(-1.0)) < 1e-12
+
+
+def test_pump_half_saturation_and_limits():
+    """Each saturating factor of j_pump is 1/2 at its threshold and tends to 1 far above it, so
+    j = rho/4 at ([Na]_i, [K]_e) = (P_Na, P_K) and j -> rho for large concentrations; j grows
+    with both concentrations."""
+    p = table2()
+    rho, PNa, PK = p["rho_pump"], p["P_Na"], p["P_K"]
+    assert membrane.pump_flux(PNa, PK, rho, PNa, PK) == pytest.approx(rho / 4, rel=1e-15)
+    assert membrane.pump_flux(1e9, 1e12, rho, PNa, PK) == pytest.approx(rho, rel=1e-9)
+    c = np.linspace(1.0, 50.0, 40)
+    assert np.all(np.diff(membrane.pump_flux(c, 4.0, rho, PNa, PK)) > 0)
+    assert np.all(np.diff(membrane.pump_flux(12.0, c, rho, PNa, PK)) > 0)
+
+
+def test_kir_factor_special_values():
+    """f_Kir at phi_M = E_K^0 (so D = B), dphi_K = -0.0185 V (so C = 2) and [K]_e = [K]_e^0 is
+    (1 + e^0.433)/2; it scales with sqrt([K]_e / [K]_e^0); it falls as dphi_K rises (inward
+    rectification: the K conductance is largest for hyperpolarised membranes)."""
+    EK0, cK0 = -0.0889, 4.0
+    assert membrane.kir_factor(cK0, -0.0185, EK0, EK0, cK0) == pytest.approx((1 + np.exp(0.433)) / 2, rel=1e-14)
+    f1 = membrane.kir_factor(cK0, 0.01, -0.07, EK0, cK0)
+    assert membrane.kir_factor(4 * cK0, 0.01, -0.07, EK0, cK0) == pytest.approx(2 * f1, rel=1e-14)
+    d = np.linspace(-0.05, 0.05, 41)
+    assert np.all(np.diff(membrane.kir_factor(cK0, d, -0.07, EK0, cK0)) < 0)
+
+
+def test_kir_pump_is_electrogenic():
+    """With every leak conductance zero the Kir-Na/K currents are the pump's alone:
+    I_Na = 3 F z_Na j, I_K = -2 F z_K j, I_Cl = 0, so the net current is F j (one charge out per
+    cycle) and I_Na / I_K = -3/2 (3 Na out, 2 K in)."""
+    from oracle import problem, system
+    from synth import make_config
+    cfg = make_config(7)
+    pb, s0 = problem.from_config(cfg)
+    pb.facet_gleak = np.zeros_like(pb.facet_gleak)
+    mf = system.membrane_fields(pb, s0)
+    I = system.channel_currents(pb, mf, s0.t)
+    j = membrane.pump_flux(s0.c_i[0, 0], s0.c_e[1, 0], pb.rho_pump, pb.P_Na, pb.P_K)
+    np.testing.assert_allclose(I.sum(axis=0), pb.F * j, rtol=1e-14)
+    np.testing.assert_allclose(I[0] / I[1], -1.5, rtol=1e-14)
+    assert np.all(I[2] == 0)

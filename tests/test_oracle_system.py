@@ -48,8 +48,12 @@ def _charges(pb, s):
     return per_cell, qe, scale
 
 
-def test_charge_conserved_per_cell_and_in_ecs():
-    cfg = make_config(4).with_nx(32)          # 16 cells, leak, per-facet g_K
+@pytest.mark.parametrize("cfg_fn", [lambda: make_config(4).with_nx(32), lambda: make_config(7)],
+                         ids=["16cells-leak-gK", "kir-bolus"])
+def test_charge_conserved_per_cell_and_in_ecs(cfg_fn):
+    # 16 cells with leak and per-facet g_K; Kir-Na/K with the electroneutral bulk source
+    # (sum_k z_k f^k = 0), which leaves every region's charge unchanged as well
+    cfg = cfg_fn()
     pb, s0 = problem.from_config(cfg)
     c0, e0, scale = _charges(pb, s0)
     s = s0
@@ -60,9 +64,10 @@ def test_charge_conserved_per_cell_and_in_ecs():
     assert abs(e1 - e0) < 1e-12 * scale
 
 
-@pytest.mark.parametrize("cfg_fn", [lambda: make_config(1), lambda: model_a(2, 16, 1e-4)])
+@pytest.mark.parametrize("cfg_fn", [lambda: make_config(1), lambda: model_a(2, 16, 1e-4), lambda: make_config(7)])
 def test_species_balance_across_membrane(cfg_fn):
-    """1^T M_r (c_r^n - c_r^{n-1}) = -+_r (1/(F z_k)) int_Gamma (dt I_ch^k + alpha_r^k C_m (phi_M^n - phi_M^{n-1}))."""
+    """1^T M_r (c_r^n - c_r^{n-1}) = -+_r (1/(F z_k)) int_Gamma (dt I_ch^k + alpha_r^k C_m (phi_M^n - phi_M^{n-1}))
+    + dt 1^T M_r f_r^{k,n} (the bulk source, switched on in the Kir workload)."""
     cfg = cfg_fn()
     pb, s0 = problem.from_config(cfg)
     A, f, mf = system.assemble(pb, s0)
@@ -77,6 +82,9 @@ def test_species_balance_across_membrane(cfg_fn):
             Wa = fem.membrane_mass(g["area"], g["fv"], g["fv"], g["n_mv"], g["n_mv"], coef=a[k][g["fv"]])
             cap = pb.Cm * (Wa @ dphiM).sum()
             rhs = -sgn * (pb.dt * ich + cap) / (pb.F * pb.z[k])
+            src = getattr(pb, "source_" + r)
+            if src is not None and pb.source_t0 < s0.t + pb.dt <= pb.source_t1:
+                rhs += pb.dt * (g["M_" + r] @ src[k]).sum()
             tot = (g["M_" + r] @ c0[k]).sum()
             assert abs(lhs - rhs) < 1e-13 * tot, (r, k, lhs, rhs)
 
