@@ -46,7 +46,7 @@ typedef int32_t knp_status;
 #define KNP_ERR_STATE          7  /* call out of order (e.g. knp_solve before knp_assemble_step) */
 
 typedef enum { KNP_HOST = 0, KNP_DEVICE = 1 } knp_memspace;
-typedef enum { KNP_MODEL_LEAK = 0, KNP_MODEL_HH = 1 } knp_membrane_model;
+typedef enum { KNP_MODEL_LEAK = 0, KNP_MODEL_HH = 1, KNP_MODEL_KIR = 2 } knp_membrane_model;
 typedef enum { KNP_STIM_NONE = 0, KNP_STIM_WINDOW = 1, KNP_STIM_PERIODIC_EXP = 2 } knp_stimulus_kind;
 typedef enum { KNP_PREC_FP64 = 0, KNP_PREC_FP32 = 1 } knp_precision;
 
@@ -113,8 +113,9 @@ typedef struct {
     double c_i0[KNP_MAX_IONS];       /* uniform initial [k]_i^0 */
     double c_e0[KNP_MAX_IONS];       /* uniform initial [k]_e^0 */
     double phi_M0;                   /* initial membrane potential; phi_i^0 = phi_M0, phi_e^0 = 0 */
-    /* membrane (Eq. 2.15 and the leak model): per facet, in knp_mesh_facets order */
-    const int32_t* facet_model;      /* host [n_facets]: KNP_MODEL_LEAK or KNP_MODEL_HH */
+    /* membrane (Eq. 2.15, the leak model and Kir-Na/K of Section 2.4.2): per facet, in
+       knp_mesh_facets order */
+    const int32_t* facet_model;      /* host [n_facets]: KNP_MODEL_LEAK, KNP_MODEL_HH or KNP_MODEL_KIR */
     const double* facet_gleak;       /* host [n_facets * n_ions] leak conductances g_leak^k */
     int32_t ion_na, ion_k;           /* ions carrying the HH Na / K channels and the stimulus (Na) */
     double gbar_na, gbar_k;          /* HH maximal conductances on HH facets */
@@ -125,6 +126,20 @@ typedef struct {
     int32_t stim_kind;               /* knp_stimulus_kind */
     double stim_gbar, stim_t0, stim_t1, stim_a, stim_tau;
     const uint8_t* stim_mask;        /* host [n_facets] (1 = stimulated) or NULL = all facets */
+    /* Kir-Na/K facets (Section 2.4.2): the K leak is g_leak^K (phi_M - E_K) f_Kir([K]_e, phi_M - E_K,
+       phi_M) with E_K^0 and [K]_e^0 taken from c_i0, c_e0 of ion_k; the Na/K pump adds
+       3 F z_Na j_pump to the Na current and -2 F z_K j_pump to the K current, with
+       j_pump = rho_pump [Na]_i^1.5 / ([Na]_i^1.5 + P_na^1.5) [K]_e / ([K]_e + P_k). Nodal at the
+       membrane vertices, P1 on the facets, like every membrane coefficient. */
+    double rho_pump;                 /* maximum pump rate, mol/(m^2 s) (Table 2: 1.115e-6) */
+    double P_na, P_k;                /* pump thresholds, mol/m^3 (Table 2: 10, 1.5) */
+    /* bulk source f_r^k (Eq. 2.1), entering f_n as dt M f_r^{k,n} (Eq. 3.5 with the dt factor):
+       host [n_vertices * n_ions] nodal values (mol/(m^3 s)) for the intracellular and the
+       extracellular copy of each vertex, or NULL = none; on for steps with source_t0 < t_n <=
+       source_t1 (t_n the end of the step) */
+    const double* source_i;
+    const double* source_e;
+    double source_t0, source_t1;
 } knp_problem_desc;
 
 /* Creates device state for one simulation on `stream`; u_0 as in Section 2.3
@@ -212,7 +227,9 @@ knp_status knp_problem_set_facet_gleak(knp_problem* prob, knp_memspace space, co
  * transposed solve is FGMRES with the same P_0 hierarchy (P_0 is symmetric, Section
  * 4.2) and the same stopping test.
  * knp_adjoint_begin zeroes the carried quantities and the accumulators (allocating the
- * adjoint work arrays on first use). */
+ * adjoint work arrays on first use); it returns KNP_ERR_INVALID_ARG for a problem with
+ * Kir-Na/K facets, whose partial derivatives are not implemented. A bulk source does not
+ * depend on the state or the conductances and needs nothing. */
 knp_status knp_adjoint_begin(knp_problem* prob);
 /* One reverse step n. Precondition: the problem's state is (u_{n-1}, w_{n-1}, t_{n-1})
  * (restore it with knp_state_set, e.g. from a checkpoint and a recomputed segment). u_n

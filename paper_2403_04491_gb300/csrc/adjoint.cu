@@ -311,6 +311,9 @@ void build_problem_stiffness(knp_problem* P, std::vector<double>& elA, std::vect
                              std::vector<int32_t>& nelist);
 
 void adjoint_begin(knp_problem* P) {
+    for (int32_t v : P->facet_model)
+        KNP_REQUIRE(v != KNP_MODEL_KIR, KNP_ERR_INVALID_ARG,
+                    "the adjoint step covers leak and HH facets; this problem has Kir-Na/K facets");
     if (!P->adj) {
         auto* W = new AdjointWork();
         P->adj = W;

@@ -79,6 +79,13 @@ __global__ void k_membrane_nodes(StepParams sp, int64_t nmv, const int32_t* __re
     }
     mf[10 * nmv + a] = w[1] * w[1] * w[1] * w[2] * (phiM - E[sp.ion_na]);
     mf[11 * nmv + a] = (w[0] * w[0]) * (w[0] * w[0]) * (phiM - E[sp.ion_k]);
+    // Kir-Na/K (Section 2.4.2): the K drive rectified by f_Kir, and the pump flux density
+    const double dK = phiM - E[sp.ion_k];
+    const double fA = 1.0 + exp(0.433), fB = 1.0 + exp(-(0.1186 + sp.EK0) / 0.0441);
+    const double fC = 1.0 + exp((dK + 0.0185) / 0.0425), fD = 1.0 + exp(-(0.1186 + phiM) / 0.0441);
+    mf[12 * nmv + a] = dK * (fA * fB / (fC * fD) * sqrt(ce[sp.ion_k] / sp.cKe0));
+    const double na15 = ci[sp.ion_na] * sqrt(ci[sp.ion_na]), pna15 = sp.P_na * sqrt(sp.P_na);
+    mf[13 * nmv + a] = sp.rho_pump * (na15 / (na15 + pna15)) * (ce[sp.ion_k] / (ce[sp.ion_k] + sp.P_k));
 }
 
 __global__ void k_elem_means(int64_t ne, int nvpe, const int32_t* __restrict__ eln, const double* __restrict__ u,
@@ -111,14 +118,15 @@ __global__ void k_row_assemble(StepParams sp, int64_t n, int64_t N_i, int32_t pi
                                int64_t n_edges, const int64_t* __restrict__ slice_ptr,
                                const int32_t* __restrict__ col, const int32_t* __restrict__ edge,
                                const double* __restrict__ msv, const double* __restrict__ ak,
-                               const double* __restrict__ u, double* __restrict__ e, double* __restrict__ f) {
+                               const double* __restrict__ u, const double* __restrict__ src, double src_dt,
+                               double* __restrict__ e, double* __restrict__ f) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const RegionCoef rc = sp.reg[r < N_i ? 0 : 1];
     int64_t s = r / SELL_C;
     int64_t base = slice_ptr[s] + r % SELL_C;
     int64_t w = (slice_ptr[s + 1] - slice_ptr[s]) / SELL_C;
-    double sum[KI] = {0, 0, 0}, fm[KI] = {0, 0, 0};
+    double sum[KI] = {0, 0, 0}, fm[KI] = {0, 0, 0}, fs[KI] = {0, 0, 0};
     int64_t dpos = -1;
     for (int64_t k = 0; k < w; ++k) {
         int64_t pos = base + k * SELL_C;
@@ -127,6 +135,8 @@ __global__ void k_row_assemble(StepParams sp, int64_t n, int64_t N_i, int32_t pi
         int64_t c = col[pos];
         double mv = msv[pos];
         for (int i = 0; i < KI; ++i) fm[i] += mv * u[4 * c + i];
+        if (src)
+            for (int i = 0; i < KI; ++i) fs[i] += mv * src[4 * c + i];
         if (ed == -1) {
             dpos = pos;
             continue;
@@ -139,7 +149,8 @@ __global__ void k_row_assemble(StepParams sp, int64_t n, int64_t N_i, int32_t pi
     }
     // the pinned phi_e column is not zeroed here: the operator kernels ignore it (see spmv.cu)
     for (int i = 0; i < KI; ++i) e[i * n_entries + dpos] = -sum[i];
-    for (int i = 0; i < KI; ++i) f[4 * r + i] = fm[i];
+    // f_r^k = M c^{k,n-1} + dt M f_r^{k,n} (the membrane terms are added by k_membrane_rhs)
+    for (int i = 0; i < KI; ++i) f[4 * r + i] = src ? fm[i] + src_dt * fs[i] : fm[i];
     f[4 * r + 3] = 0.0;
 }
 
@@ -189,7 +200,7 @@ __global__ void k_membrane_rhs(StepParams sp, int64_t nmv, int dim, int32_t pin,
         int64_t fid = mvf[q] >> 2;
         int s = mvf[q] & 3;
         double A = area[fid];
-        bool hh = fmodel[fid] == KNP_MODEL_HH;
+        const bool hh = fmodel[fid] == KNP_MODEL_HH, kir = fmodel[fid] == KNP_MODEL_KIR;
         double gst = fmask[fid] ? sp.g_stim : 0.0;
         double gl[KI];
         for (int k = 0; k < KI; ++k) gl[k] = fgleak[fid * KI + k];
@@ -202,6 +213,12 @@ __global__ void k_membrane_rhs(StepParams sp, int64_t nmv, int dim, int32_t pin,
             if (hh) {
                 I[sp.ion_na] += sp.gbar_na * mf[10 * nmv + mc];
                 I[sp.ion_k] += sp.gbar_k * mf[11 * nmv + mc];
+            }
+            if (kir) {
+                // rectified K leak and the pump: 3 F z_Na j out of Na, -2 F z_K j in K
+                const double j = mf[13 * nmv + mc];
+                I[sp.ion_k] = gl[sp.ion_k] * mf[12 * nmv + mc] - 2.0 * sp.F * sp.z[sp.ion_k] * j;
+                I[sp.ion_na] += 3.0 * sp.F * sp.z[sp.ion_na] * j;
             }
             for (int k = 0; k < KI; ++k) intI[k] += Mcs * I[k];
             intPhi += Mcs * mf[mc];
@@ -257,9 +274,13 @@ void launch_assembly(knp_problem* P) {
     if (P->n_edges)
         k_edge_values<<<nblk(P->n_edges), 256, 0, st>>>(P->n_edges, P->n_elem, P->eptr.p, P->einc.p, P->ecoef.p,
                                                         P->cbar.p, P->ak.p);
+    // the bulk source of the step's end time t_n, if any
+    const double t_n = P->t + sp.dt;
+    const double* src =
+        (P->src.p && P->desc.source_t0 < t_n && t_n <= P->desc.source_t1) ? P->src.p : nullptr;
     k_row_assemble<<<nblk(n, 128), 128, 0, st>>>(sp, n, P->N_i, P->pin, P->sell.n_entries, P->n_edges,
                                             P->sell.slice_ptr.p, P->sell.col.p, P->sell_edge.p, P->sell_m.p,
-                                            P->ak.p, P->u.p, P->sell_e.p, P->f.p);
+                                            P->ak.p, P->u.p, src, sp.dt, P->sell_e.p, P->f.p);
     if (P->n_pairs)
         k_membrane_pairs<<<nblk(P->n_pairs, 128), 128, 0, st>>>(P->n_pairs, nmv, P->dim, P->pin, P->sell.n_entries,
                                                            (int64_t)P->h_xcol.size(), P->mp_ptr.p, P->mpf.p,

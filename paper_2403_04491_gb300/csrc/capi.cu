@@ -78,8 +78,27 @@ knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc
         const int64_t nf = mesh->nf();
         P->facet_model.assign(desc->facet_model, desc->facet_model + nf);
         P->facet_gleak.assign(desc->facet_gleak, desc->facet_gleak + nf * KI);
-        for (int32_t v : P->facet_model)
-            KNP_REQUIRE(v == KNP_MODEL_LEAK || v == KNP_MODEL_HH, KNP_ERR_INVALID_ARG, "unknown membrane model %d", v);
+        bool kir = false;
+        for (int32_t v : P->facet_model) {
+            KNP_REQUIRE(v == KNP_MODEL_LEAK || v == KNP_MODEL_HH || v == KNP_MODEL_KIR, KNP_ERR_INVALID_ARG,
+                        "unknown membrane model %d", v);
+            kir |= v == KNP_MODEL_KIR;
+        }
+        if (kir)
+            KNP_REQUIRE(desc->rho_pump >= 0 && desc->P_na > 0 && desc->P_k > 0 && desc->c_i0[desc->ion_k] > 0 &&
+                            desc->c_e0[desc->ion_k] > 0,
+                        KNP_ERR_INVALID_ARG, "Kir-Na/K facets need rho_pump >= 0, P_na, P_k > 0 and positive K "
+                                             "initial concentrations");
+        const int64_t nv = mesh->nv;
+        const double* srcs[2] = {desc->source_i, desc->source_e};
+        for (int r = 0; r < 2; ++r) {
+            if (!srcs[r]) continue;
+            P->source_v[r].assign(srcs[r], srcs[r] + nv * KI);
+            for (double v : P->source_v[r])
+                KNP_REQUIRE(std::isfinite(v), KNP_ERR_INVALID_ARG, "bulk source is not finite");
+        }
+        KNP_REQUIRE(!(srcs[0] || srcs[1]) || desc->source_t1 >= desc->source_t0, KNP_ERR_INVALID_ARG,
+                    "source_t1 < source_t0");
         if (desc->stim_mask)
             P->stim_mask.assign(desc->stim_mask, desc->stim_mask + nf);
         else
@@ -87,6 +106,8 @@ knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc
         P->desc.facet_model = nullptr;
         P->desc.facet_gleak = nullptr;
         P->desc.stim_mask = nullptr;
+        P->desc.source_i = nullptr;
+        P->desc.source_e = nullptr;
         StepParams& sp = P->sp;
         for (int k = 0; k < KI; ++k) sp.z[k] = desc->z[k];
         sp.R = desc->R;
@@ -107,6 +128,13 @@ knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc
         sp.gbar_k = desc->gbar_k;
         sp.phi_rest = desc->phi_rest;
         sp.n_ode = desc->n_ode;
+        sp.rho_pump = desc->rho_pump;
+        sp.P_na = desc->P_na;
+        sp.P_k = desc->P_k;
+        sp.cKe0 = desc->c_e0[desc->ion_k];
+        sp.EK0 = (kir) ? desc->R * desc->T / (desc->F * desc->z[desc->ion_k]) *
+                             std::log(desc->c_e0[desc->ion_k] / desc->c_i0[desc->ion_k])
+                       : 0.0;
         build_problem(P.get());
         *out = P.release();
     });

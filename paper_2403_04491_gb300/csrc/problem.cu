@@ -407,7 +407,7 @@ void build_problem(knp_problem* P) {
     P->mv_g.upload(h_mvg, st);
     P->gates.alloc(3 * nmv);
     P->gates_new.alloc(3 * nmv);
-    P->mfield.alloc(12 * nmv);
+    P->mfield.alloc(14 * nmv);
     P->f_mv.upload(h_fmv, st);
     P->f_area.upload(h_farea, st);
     P->f_model.upload(P->facet_model, st);
@@ -418,6 +418,19 @@ void build_problem(knp_problem* P) {
     P->mp_ptr.upload(h_mp_ptr, st);
     P->mpf.upload(h_mpf, st);
     P->mp_tgt.upload(h_tgt, st);
+    if (!P->source_v[0].empty() || !P->source_v[1].empty()) {
+        // bulk source at the nodes: the vertex's intracellular values for i-nodes, its
+        // extracellular values for e-nodes
+        std::vector<double> hs(4 * n, 0.0);
+        for (int r = 0; r < 2; ++r) {
+            if (P->source_v[r].empty()) continue;
+            const std::vector<int32_t>& verts = r == 0 ? m.nodes_i : m.nodes_e;
+            const int64_t off = r == 0 ? 0 : Ni;
+            for (size_t j = 0; j < verts.size(); ++j)
+                for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)verts[j] * KI + k];
+        }
+        P->src.upload(hs, st);
+    }
     P->u.alloc(4 * n);
     P->f.alloc(4 * n);
     P->f.zero(st);

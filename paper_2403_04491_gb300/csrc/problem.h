@@ -81,6 +81,8 @@ struct StepParams {
     double gbar_na, gbar_k, phi_rest;
     int32_t n_ode;
     double g_stim;         // stimulus conductance at t_{n-1}
+    // Kir-Na/K (Section 2.4.2): pump constants, E_K^0 and [K]_e^0
+    double rho_pump, P_na, P_k, EK0, cKe0;
 };
 
 struct AmgHierarchy;        // vcycle.cu
@@ -97,6 +99,7 @@ struct knp_problem {
     std::vector<int32_t> facet_model;
     std::vector<double> facet_gleak;
     std::vector<uint8_t> stim_mask;
+    std::vector<double> source_v[2];     // bulk source per vertex [n_vertices][n_ions] (i, e); empty = none
     int32_t dim = 0;
     int64_t N_i = 0, N_e = 0, n_nodes = 0, n_mv = 0, nf = 0, n_elem = 0, n_edges = 0, n_pairs = 0, n_edge_inc = 0;
     int32_t pin = -1;               // global node of the pinned phi_e
@@ -125,7 +128,8 @@ struct knp_problem {
     knp::DArray<int32_t> mv_g;           // [2][n_mv] global i-node and e-node of each membrane vertex
     knp::DArray<double> gates;           // [3][n_mv] (n, m, h) of the committed state w_{n-1}
     knp::DArray<double> gates_new;       // [3][n_mv] w_n computed by the last assembly
-    knp::DArray<double> mfield;          // [12][n_mv]: phiM, C_i(3), C_e(3), q_leak(3), q_hhna, q_hhk
+    knp::DArray<double> mfield;          // [14][n_mv]: phiM, C_i(3), C_e(3), q_leak(3), q_hhna, q_hhk,
+                                         // q_kir (Kir-rectified K drive), j_pump
     knp::DArray<int32_t> f_mv;           // [nf][dim] membrane-vertex index of facet vertices
     knp::DArray<double> f_area;
     knp::DArray<int32_t> f_model;
@@ -141,6 +145,7 @@ struct knp_problem {
     knp::DArray<double> sinv;            // 1/sqrt(diag P_0) (set by knp_amg_setup)
     knp::DArray<double> svec;            // sqrt(diag P_0)
     knp::DArray<double> swt;             // weights of the stopping test: svec, 0 on the pinned phi_e
+    knp::DArray<double> src;             // bulk source f_r^k at the nodes [n_nodes][4] (empty = none)
 
     knp::Profiler prof;
     knp::AmgHierarchy* amg = nullptr;

@@ -52,7 +52,10 @@ class ProblemDesc(C.Structure):
                 ("gbar_na", C.c_double), ("gbar_k", C.c_double), ("phi_rest", C.c_double),
                 ("w0", C.c_double * 3), ("n_ode", C.c_int32), ("stim_kind", C.c_int32),
                 ("stim_gbar", C.c_double), ("stim_t0", C.c_double), ("stim_t1", C.c_double),
-                ("stim_a", C.c_double), ("stim_tau", C.c_double), ("stim_mask", C.POINTER(C.c_uint8))]
+                ("stim_a", C.c_double), ("stim_tau", C.c_double), ("stim_mask", C.POINTER(C.c_uint8)),
+                ("rho_pump", C.c_double), ("P_na", C.c_double), ("P_k", C.c_double),
+                ("source_i", C.POINTER(C.c_double)), ("source_e", C.POINTER(C.c_double)),
+                ("source_t0", C.c_double), ("source_t1", C.c_double)]
 
 
 class AmgOpts(C.Structure):
@@ -234,8 +237,20 @@ class Problem:
             for k, v in enumerate(desc[key]):
                 arr[k] = float(v)
         for key in ("R", "T", "F", "Cm", "dt", "phi_M0", "gbar_na", "gbar_k", "phi_rest", "stim_gbar", "stim_t0",
-                    "stim_t1", "stim_a", "stim_tau"):
+                    "stim_t1", "stim_a", "stim_tau", "source_t0", "source_t1"):
             setattr(d, key, float(desc.get(key, 0.0)))
+        # Kir-Na/K pump constants (Table 2 values unless given)
+        d.rho_pump = float(desc.get("rho_pump", 1.115e-6))
+        d.P_na = float(desc.get("P_na", 10.0))
+        d.P_k = float(desc.get("P_k", 1.5))
+        # bulk source per vertex [n_vertices][n_ions] for the i and e copies (None = none)
+        nv = mesh.info["n_vertices"]
+        self._source = {}
+        for key in ("source_i", "source_e"):
+            v = desc.get(key)
+            if v is not None:
+                self._source[key] = np.ascontiguousarray(v, dtype=np.float64).reshape(nv, n_ions)
+                setattr(d, key, _dptr(self._source[key]))
         for k, v in enumerate(desc["w0"]):
             d.w0[k] = float(v)
         d.ion_na = int(desc.get("ion_na", 0))
@@ -439,5 +454,6 @@ def problem_from_config(cfg, stream=None, mesh: Mesh = None):
                 ion_na=0, ion_k=1, gbar_na=p["gbar_Na"], gbar_k=p["gbar_K"], phi_rest=p["phi_rest"],
                 w0=(p["n0"], p["m0"], p["h0"]), n_ode=25, stim_kind=cfg.stim_kind, stim_gbar=cfg.stim_gbar,
                 stim_t0=cfg.stim_t0, stim_t1=cfg.stim_t1, stim_a=cfg.stim_a, stim_tau=cfg.stim_tau,
-                stim_mask=mask)
+                stim_mask=mask, rho_pump=p["rho_pump"], P_na=p["P_Na"], P_k=p["P_K"],
+                source_e=cfg.vertex_source_e(), source_t0=cfg.source_t0, source_t1=cfg.source_t1)
     return mesh, Problem(mesh, desc, stream=stream)

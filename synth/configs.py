@@ -127,16 +127,17 @@ def make_config(i: int) -> Config:
                       stim_gbar=40.0, stim_t0=0.0, stim_t1=1e-3, stim_xmax=0.4 * L)
     if i == 6:
         # Kir-Na/K membrane with a K bolus and Na removal in the extracellular half x < L/2 for
-        # 0 < t <= 2 ms (Section 5.2's stimulus on a Model-A-shaped box; Table 2 leak values)
+        # 0 < t <= 2 ms (Section 5.2's stimulus on a Model-A-shaped box; Table 2 leak values); the
+        # window ends half a step after 2 ms so that the accumulated t_20 = 2 ms (+ rounding) is in
         lo, hi = _single(3, 0.3, 0.7)
         return Config("kir-3d-64-bolus", 3, 64, L, lo, hi, MODEL_KIR, (1.0, 4.0, 0.0),
                       dt=1e-4, n_steps=50, rtol=1e-10, source_e=(-1.0, 1.0, 0.0), source_xmax=0.5 * L,
-                      source_t0=0.0, source_t1=2e-3)
+                      source_t0=0.0, source_t1=2e-3 + 0.5e-4)
     if i == 7:
         lo, hi = _single(2, 0.25, 0.75)
         return Config("kir-2d-32-bolus", 2, 32, L, lo, hi, MODEL_KIR, (1.0, 4.0, 0.0),
                       dt=1e-4, n_steps=30, rtol=1e-10, source_e=(-1.0, 1.0, 0.0), source_xmax=0.5 * L,
-                      source_t0=0.0, source_t1=2e-3)
+                      source_t0=0.0, source_t1=2e-3 + 0.5e-4)
     raise ValueError(i)
 
 

@@ -113,3 +113,13 @@ def test_autograd_function_with_checkpoints():
     Ni = pb.topo.N_i
     assert _rel(gK.grad.numpy(), ref["grad_gleak"][:, 1]) < 1e-5
     assert _rel(cK.grad.numpy(), ref["dLdu0"][Ni:2 * Ni]) < 1e-5
+
+
+def test_adjoint_rejects_kir_facets():
+    """The adjoint's partial derivatives cover leak and HH facets; Kir-Na/K facets are refused."""
+    from paper_2403_04491_gb300 import problem_from_config
+    from paper_2403_04491_gb300.knp import KnpError
+    _, prob = problem_from_config(make_config(7))
+    prob.amg_setup()
+    with pytest.raises(KnpError, match="Kir"):
+        prob.adjoint_begin()

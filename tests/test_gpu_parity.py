@@ -31,6 +31,9 @@ def _cfgs():
         "cfg1-2d-leak": make_config(1),
         "cfg2-3d-hh-16": make_config(2).with_nx(16),
         "cfg4-2d-16cells-32": make_config(4).with_nx(32),
+        # Kir-Na/K membrane with the extracellular K bolus (on for 0 < t_n <= 2 ms)
+        "kir-2d-32": make_config(7),
+        "kir-3d-16": make_config(6).with_nx(16),
     }
 
 
@@ -56,7 +59,8 @@ def test_assembly_and_operator(name):
     assert np.all(prob.operator_entries(r[off], c[off]) == 0)
 
 
-STEP_CASES = [("cfg1-2d-leak", 10, "direct"), ("cfg2-3d-hh-16", 8, "lu_p0"), ("cfg4-2d-16cells-32", 5, "direct")]
+STEP_CASES = [("cfg1-2d-leak", 10, "direct"), ("cfg2-3d-hh-16", 8, "lu_p0"), ("cfg4-2d-16cells-32", 5, "direct"),
+              ("kir-2d-32", 24, "direct"), ("kir-3d-16", 6, "lu_p0")]
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64-amg", "fp32-amg"])
