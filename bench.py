@@ -45,23 +45,26 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7],
                     help="workload: 2 (default, the headline), 1 (2D leak), 3 (125-cell 3D, FP32 hierarchy, "
-                         "rtol 1e-8), 4 (16-cell 2D)")
+                         "rtol 1e-8), 4 (16-cell 2D), 5 (512-cell 256^3, FP32 hierarchy, rtol 1e-8), "
+                         "6 (Kir-Na/K 64^3 with a K bolus), 7 (Kir-Na/K 2D)")
     ap.add_argument("--nx", type=int, default=None, help="override the mesh resolution of the workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time a checkpointed forward + adjoint run of the 16-cell 2D workload (KNPFunction)")
     args = ap.parse_args()
-    if args.config == 3 and "--precision" not in sys.argv:
+    if args.config in (3, 5) and "--precision" not in sys.argv:
         args.precision = "fp32"
-    if args.config == 3 and "--rtol" not in sys.argv:
+    if args.config in (3, 5) and "--rtol" not in sys.argv:
         args.rtol = 1e-8
     return args
 
 
 def workload_name(cfg, n_dof):
+    membrane = {0: "leak", 1: "HH", 2: "Kir-Na/K"}[cfg.model]
+    src = "" if cfg.source_e is None else ", extracellular K bolus / Na removal for x < L/2, 0 < t <= 2 ms"
     return (f"{cfg.name}: {cfg.dim}D, {cfg.nx}^{cfg.dim} mesh, {len(cfg.cell_lo)} cell(s), {n_dof:,} DOF, "
-            f"dt {cfg.dt * 1e3:g} ms, {'HH' if cfg.model == 1 else 'leak'} membrane")
+            f"dt {cfg.dt * 1e3:g} ms, {membrane} membrane{src}")
 
 
 # --------------------------------------------------------------------------- oracle legs
@@ -246,6 +249,12 @@ def slowest_rank_ms(ms, world, device):
     return float(t.item())
 
 
+def host_peak_rss_gb():
+    """Peak resident host memory of this process so far (mesh generation, topology, setup)."""
+    import resource
+    return resource.getrusage(resource.RUSAGE_SELF).ru_maxrss * 1024 / 1e9
+
+
 def job_value(n_dof, steps, world, ms):
     """DOF x steps of all replicas per second of the slowest rank's time."""
     return n_dof * steps * world / (ms / 1e3)
@@ -426,7 +435,7 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 iters_per_step=float(np.mean(iters)), iters=iters, setup_s=dict(create=t_create, amg=t_amg),
                 amg=prob.amg_info(), gpu_launches=launches, clocks=clocks, roofline=roof,
-                device_memory_gb=mem_gb,
+                device_memory_gb=mem_gb, host_peak_rss_gb=host_peak_rss_gb(),
                 e2e=e2e, cpu_baseline=cpu, mixed=mixed)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -88,13 +88,15 @@ def box_cells(n_per_side: int, side: float, gap: float, dim: int, jitter=None, r
     return np.array(lows), np.array(highs)
 
 
-def tag_elements(coords_idx_centroid: np.ndarray, boxes: np.ndarray) -> np.ndarray:
-    """Tag each element by the snapped box that contains its centroid (grid units)."""
-    tag = np.zeros(coords_idx_centroid.shape[0], dtype=np.int32)
+def tag_grid_boxes(dim: int, nx: int, boxes: np.ndarray) -> np.ndarray:
+    """Tag of every grid box (flattened with x fastest): the last snapped cell box [lo, hi]
+    (grid units) that contains it, 0 if none. A simplex lies in one grid box, and its centroid
+    is strictly inside a snapped cell box exactly when its grid box is, so this is the tag of
+    every simplex of that grid box."""
+    tag = np.zeros((nx,) * dim, dtype=np.int32)          # axes (z, y, x) / (y, x)
     for j, (lo, hi) in enumerate(boxes):
-        inside = np.all((coords_idx_centroid > lo) & (coords_idx_centroid < hi), axis=1)
-        tag[inside] = j + 1
-    return tag
+        tag[tuple(slice(int(lo[a]), int(hi[a])) for a in range(dim)[::-1])] = j + 1
+    return tag.reshape(-1)
 
 
 def make_mesh(dim: int, nx: int, length: float, lo, hi) -> StructuredMesh:
@@ -104,6 +106,7 @@ def make_mesh(dim: int, nx: int, length: float, lo, hi) -> StructuredMesh:
         raise ValueError("a cell snapped to zero width")
     if np.any(boxes[:, 0] < 1) or np.any(boxes[:, 1] > nx - 1):
         raise ValueError("cells must stay inside the domain interior")
-    centroid = coords[elems].mean(axis=1) / length * nx
-    tag = tag_elements(centroid, boxes)
+    # structured_mesh emits the simplices of one grid box consecutively, grid boxes x fastest
+    per_box = elems.shape[0] // nx ** dim
+    tag = np.repeat(tag_grid_boxes(dim, nx, boxes), per_box)
     return StructuredMesh(dim, nx, coords, elems, tag, boxes, length)
