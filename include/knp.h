@@ -167,6 +167,11 @@ typedef struct {
     double theta_coarse;        /* strength threshold on levels >= 1 (< 0: same as theta; 0) */
     double p_drop;              /* drop prolongator entries below p_drop x the row's largest (0: keep all) */
     int32_t host_setup;         /* 1: build the hierarchy on the host (reference path); 0: on the GPU */
+    int32_t inner_cg_max_it;    /* 0: P_0^{-1} is one V-cycle (AMG(P_0), Section 4.2). > 0: CG(P_0) of
+                                   Section 6.3: each of the 2(|K|+1) field blocks of P_0 is solved by
+                                   CG preconditioned with the V-cycle, to inner_cg_rtol or this many
+                                   iterations (FP64 hierarchy only) */
+    double inner_cg_rtol;       /* relative residual of each block's CG */
 } knp_amg_opts;
 
 /* Smoothed-aggregation AMG on P_0 (Eq. 4.4) assembled from the initial
@@ -194,6 +199,7 @@ typedef struct {
     int32_t restarts;
     double true_relres;    /* scaled true residual ||S^-1 (f - A u)|| / ||S^-1 f|| at exit */
     double ms;             /* wall time of the solve (host clock, includes synchronisation) */
+    int64_t inner_iterations;  /* inner CG iterations of CG(P_0) over the solve (0 for AMG(P_0)) */
 } knp_solve_stats;
 
 /* FGMRES(restart), FP64, x_0 = u_{n-1} (Section 6.2), right-preconditioned by

@@ -62,6 +62,7 @@ knp_problem::~knp_problem() {
     delete amg;
     gmres_free(gw);
     adjoint_free(adj);
+    pcg_free(pcg);
 }
 
 extern "C" {
@@ -162,6 +163,10 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
                         o->cheb_degree >= 1 && o->cheb_degree <= 8 && o->cheb_ratio > 1 && o->theta_coarse < 1 &&
                         o->p_drop >= 0 && o->p_drop < 1,
                     KNP_ERR_INVALID_ARG, "AMG options out of range");
+        KNP_REQUIRE(o->inner_cg_max_it >= 0 && (o->inner_cg_max_it == 0 || (o->inner_cg_rtol > 0 && o->inner_cg_rtol < 1)),
+                    KNP_ERR_INVALID_ARG, "inner CG options out of range");
+        KNP_REQUIRE(o->inner_cg_max_it == 0 || o->precision == KNP_PREC_FP64, KNP_ERR_INVALID_ARG,
+                    "CG(P_0) needs the FP64 hierarchy");
         if (!p->assembled) launch_assembly(p);
         cudaStream_t st = p->stream;
         std::vector<double> m, a, e;
@@ -215,6 +220,8 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
         if (o->host_setup || !amg_build_gpu(A0, strength, p->pin, so, H, st, amg_host_spgemm))
             amg_build(A0, strength, p->pin, so, H);
         amg_upload(p, H, o->precision, o->cheb_degree);
+        p->amg->inner_cg_max_it = o->inner_cg_max_it;
+        p->amg->inner_cg_rtol = o->inner_cg_rtol;
         KNP_CUDA(cudaMemcpyAsync(p->svec.p, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         KNP_CUDA(cudaMemcpyAsync(p->sinv.p, si.data(), si.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         // the pinned row is an identity whose scale says nothing about the solution: leave it out

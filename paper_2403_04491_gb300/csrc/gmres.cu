@@ -360,6 +360,8 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     const int m = o.restart;
     KNP_REQUIRE(m >= 1 && m + 2 <= MAXV, KNP_ERR_INVALID_ARG, "restart must be in [1, %d]", MAXV - 2);
     GmresWork& g = *gmres_work(p, m);
+    KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
+    const int64_t inner0 = p->amg->inner_its;
     cudaStream_t st = p->stream;
     const int64_t n4 = g.n4;
     const unsigned nb = (unsigned)((n4 + 255) / 256);
@@ -425,8 +427,8 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         for (int j = 0; j <= m; ++j) {
             double* vj = g.V.p + (int64_t)j * n4;
             double* zj = g.Z.p + (int64_t)j * n4;
-            // z_j = V-cycle(S v_j), unless the previous step queued it
-            if (!vc_queued) vcycle_apply(p, vj, p->svec.p, zj);
+            // z_j = P_0^{-1} (S v_j) (one V-cycle, or CG(P_0)), unless the previous step queued it
+            if (!vc_queued) precond_apply(p, vj, p->svec.p, zj);
             vc_queued = false;
             const bool arnoldi = (j < m) && (its < o.max_it);
             bool check = last_check < 0 || !arnoldi || j - last_check >= CHECK_EVERY;
@@ -489,7 +491,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
             if (arnoldi) {
                 // v_{j+1} is already normalised on the device: queue its V-cycle before the host
                 // waits for this step's dots, so the GPU works while the host does the Givens step
-                vcycle_apply(p, g.V.p + (int64_t)(j + 1) * n4, p->svec.p, g.Z.p + (int64_t)(j + 1) * n4);
+                precond_apply(p, g.V.p + (int64_t)(j + 1) * n4, p->svec.p, g.Z.p + (int64_t)(j + 1) * n4);
                 vc_queued = true;
             }
             KNP_CUDA(cudaEventSynchronize(g.ev_dots));
@@ -580,6 +582,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     res.relres = relres;
     stats.iterations = its;
     stats.restarts = restarts;
+    stats.inner_iterations = p->amg->inner_its - inner0;
     stats.true_relres = relres;
     stats.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return res;

@@ -88,6 +88,7 @@ struct StepParams {
 struct AmgHierarchy;        // vcycle.cu
 struct GmresWork;           // gmres.cu
 struct AdjointWork;         // adjoint.cu
+struct PcgWork;             // pcg.cu
 
 }  // namespace knp
 
@@ -151,6 +152,7 @@ struct knp_problem {
     knp::AmgHierarchy* amg = nullptr;
     knp::GmresWork* gw = nullptr;
     knp::AdjointWork* adj = nullptr;
+    knp::PcgWork* pcg = nullptr;
     ~knp_problem();
 };
 
@@ -160,6 +162,7 @@ void launch_assembly(knp_problem* p);
 double stimulus_at(const knp_problem_desc& d, double t);
 // adjoint.cu
 void adjoint_free(AdjointWork* w);
+void pcg_free(PcgWork* w);
 void adjoint_begin(knp_problem* P);
 void adjoint_step(knp_problem* P, bool device, const double* u_n, const double* dLdu, const knp_solve_opts& o,
                   knp_solve_stats& stats);

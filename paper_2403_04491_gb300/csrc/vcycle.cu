@@ -186,6 +186,18 @@ __global__ void __launch_bounds__(128) k_resid_sell(int64_t n, const int64_t* __
     bb.store(r + 4 * i);
 }
 
+// y = A x on a sliced-ELL level
+template <class T>
+__global__ void __launch_bounds__(128) k_sell_apply(int64_t n, const int64_t* __restrict__ sp,
+                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                    const T* __restrict__ x, T* __restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T acc[4];
+    sell_row<T>(i, sp, col, val, x, acc);
+    V4<T>{{acc[0], acc[1], acc[2], acc[3]}}.store(y + 4 * i);
+}
+
 template <class T, int S>
 __global__ void __launch_bounds__(128) k_resid_csr(int64_t n, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
@@ -502,6 +514,15 @@ static void vcycle_launch(knp_problem* p, const double* v, const double* s, doub
 // problem's stream. Each replay starts from
 // scratch (the first kernel writes b, x and d of the finest level), so replays are independent.
 // While a kernel class is being profiled the launches go out one by one.
+void p0_apply(knp_problem* p, const double* x, double* y) {
+    KNP_REQUIRE(p->amg && p->amg->h64, KNP_ERR_STATE, "P_0 products need the FP64 hierarchy");
+    DevLevel<double>& L = *static_cast<AmgDev<double>*>(p->amg->h64)->L[0];
+    KNP_REQUIRE(L.sell, KNP_ERR_STATE, "the finest level is not sliced ELL");
+    count_launch();
+    k_sell_apply<double><<<nblk(L.n, 128), 128, 0, p->stream>>>(L.n, L.sp.p, L.scol.p, L.sval.p, x, y);
+    KNP_CUDA(cudaGetLastError());
+}
+
 void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
     KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
     AmgHierarchy& H = *p->amg;

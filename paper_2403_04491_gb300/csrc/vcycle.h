@@ -25,10 +25,18 @@ struct AmgHierarchy {
     bool use_graphs = true;
     cudaStream_t gstream = nullptr;
     std::map<std::tuple<const double*, const double*, double*>, VcycleGraph> graphs;
+    // CG(P_0): P_0^{-1} applied by V-cycle-preconditioned CG per field block (0 = one V-cycle)
+    int inner_cg_max_it = 0;
+    double inner_cg_rtol = 0.0;
+    int64_t inner_its = 0;   // inner CG iterations so far
     ~AmgHierarchy();
 };
 
 void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degree);
 void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z);
+// y = P_0 x with the finest level of the FP64 hierarchy; x, y [n][4] doubles on the device
+void p0_apply(knp_problem* p, const double* x, double* y);
+// z = P_0^{-1} (s .* v): one V-cycle, or CG(P_0) when the hierarchy was set up for it
+void precond_apply(knp_problem* p, const double* v, const double* s, double* z);
 
 }  // namespace knp

@@ -61,7 +61,8 @@ class ProblemDesc(C.Structure):
 class AmgOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("theta", C.c_double), ("coarse_max", C.c_int32),
                 ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("cheb_ratio", C.c_double),
-                ("theta_coarse", C.c_double), ("p_drop", C.c_double), ("host_setup", C.c_int32)]
+                ("theta_coarse", C.c_double), ("p_drop", C.c_double), ("host_setup", C.c_int32),
+                ("inner_cg_max_it", C.c_int32), ("inner_cg_rtol", C.c_double)]
 
 
 class SolveOpts(C.Structure):
@@ -69,7 +70,8 @@ class SolveOpts(C.Structure):
 
 
 class SolveStats(C.Structure):
-    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("true_relres", C.c_double), ("ms", C.c_double)]
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("true_relres", C.c_double), ("ms", C.c_double),
+                ("inner_iterations", C.c_int64)]
 
 
 class ProblemInfo(C.Structure):
@@ -276,16 +278,20 @@ class Problem:
         _check(_lib.knp_assemble_step(self.handle))
 
     def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=1,
-                  cheb_ratio=4.0, theta_coarse=0.0, p_drop=0.0, host_setup=False):
+                  cheb_ratio=4.0, theta_coarse=0.0, p_drop=0.0, host_setup=False, inner_cg_max_it=0,
+                  inner_cg_rtol=1e-8):
+        """inner_cg_max_it > 0 selects CG(P_0) (V-cycle-preconditioned CG per field block of P_0,
+        to inner_cg_rtol) instead of one V-cycle."""
         o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop,
-                    int(host_setup))
+                    int(host_setup), int(inner_cg_max_it), float(inner_cg_rtol))
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
     def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):
         o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
         s = SolveStats()
         _check(_lib.knp_solve(self.handle, C.byref(o), C.byref(s)))
-        return {"iterations": s.iterations, "restarts": s.restarts, "true_relres": s.true_relres, "ms": s.ms}
+        return {"iterations": s.iterations, "restarts": s.restarts, "true_relres": s.true_relres, "ms": s.ms,
+                "inner_iterations": s.inner_iterations}
 
     def step(self, nsteps=1, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):
         o = SolveOpts(rtol, restart, max_it, int(phi_e_group))

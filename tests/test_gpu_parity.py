@@ -163,3 +163,52 @@ def test_gpu_amg_setup_matches_host_setup(precision):
     sa = a.step(2, rtol=1e-10)
     sb = b.step(2, rtol=1e-10)
     assert [s["iterations"] for s in sa] == [s["iterations"] for s in sb]
+
+
+@pytest.mark.parametrize("name", ["cfg2-3d-hh-16", "kir-3d-16"])
+def test_time_dependent_preconditioner(name):
+    """P_n rebuilt from the current state before every step (Eq. 4.4 at step n) against P_0 reused
+    for all steps (Section 4.2): both runs match the oracle, and reusing P_0 costs at most a
+    couple of iterations per step (the paper reports little or no impact)."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = _cfgs()[name]
+    n_steps = 6
+    pb, ref = oracle_run(cfg, n_steps, "lu_p0")
+    its = {}
+    for refresh in (False, True):
+        _, prob = problem_from_config(cfg)
+        prob.amg_setup()
+        its[refresh] = []
+        for n in range(1, n_steps + 1):
+            if refresh and n > 1:
+                prob.amg_setup()
+            st = prob.step(1, rtol=1e-10)
+            its[refresh].append(st[0]["iterations"])
+            ec, ep = rel_errors(prob.state_get(), ref[n])
+            assert ec <= TOL and ep <= TOL, (refresh, n, ec, ep)
+    print(name, "iterations with P_0 reused:", its[False], "with P_n:", its[True])
+    assert np.mean(its[False]) <= np.mean(its[True]) + 2.0
+
+
+def test_cg_p0_inner_solve():
+    """CG(P_0) of Section 6.3: each field block of P_0 solved by V-cycle-preconditioned CG to
+    1e-10 instead of one V-cycle. The steps match the oracle, and FGMRES needs no more iterations
+    than with the single V-cycle (it now sees P_0^{-1} itself)."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = _cfgs()["cfg2-3d-hh-16"]
+    n_steps = 3
+    pb, ref = oracle_run(cfg, n_steps, "lu_p0")
+    its = {}
+    for inner in (0, 60):
+        _, prob = problem_from_config(cfg)
+        prob.amg_setup(inner_cg_max_it=inner, inner_cg_rtol=1e-10)
+        its[inner] = []
+        for n in range(1, n_steps + 1):
+            prob.assemble_step()
+            st = prob.solve(rtol=1e-10)
+            its[inner].append(st["iterations"])
+            assert (st["inner_iterations"] > 0) == (inner > 0)
+            ec, ep = rel_errors(prob.state_get(), ref[n])
+            assert ec <= TOL and ep <= TOL, (inner, n, ec, ep)
+    print("FGMRES iterations, AMG(P_0):", its[0], "CG(P_0):", its[60])
+    assert sum(its[60]) <= sum(its[0])
