@@ -62,13 +62,14 @@ class Config:
     source_xmax: float = np.inf       # vertices with x < source_xmax (metres), switched on
     source_t0: float = 0.0            # for source_t0 < t_n <= source_t1
     source_t1: float = 0.0
+    refine: Optional[tuple] = None    # (ratio, width): interface refinement of the tensor grid
     params: dict = field(default_factory=table2)
     _mesh: Optional[StructuredMesh] = None
 
     @property
     def mesh(self) -> StructuredMesh:
         if self._mesh is None:
-            self._mesh = make_mesh(self.dim, self.nx, self.length, self.cell_lo, self.cell_hi)
+            self._mesh = make_mesh(self.dim, self.nx, self.length, self.cell_lo, self.cell_hi, self.refine)
         return self._mesh
 
     def elem_facet_xi(self) -> np.ndarray:
@@ -138,6 +139,13 @@ def make_config(i: int) -> Config:
         return Config("kir-2d-32-bolus", 2, 32, L, lo, hi, MODEL_KIR, (1.0, 4.0, 0.0),
                       dt=1e-4, n_steps=30, rtol=1e-10, source_e=(-1.0, 1.0, 0.0), source_xmax=0.5 * L,
                       source_t0=0.0, source_t1=2e-3 + 0.5e-4)
+    if i == 8:
+        # the 3D HH workload on a 32^3 grid whose intervals next to the cell faces are cut into 4
+        # slabs (Section 6.4's interface-based refinement, here on a tensor grid): 44^3 grid boxes
+        lo, hi = _single(3, 0.3, 0.7)
+        return Config("hh-3d-32-interface-refined", 3, 32, L, lo, hi, MODEL_HH, (0.2, 0.8, 0.0),
+                      dt=5e-5, n_steps=100, rtol=1e-10, stim_kind=STIM_WINDOW,
+                      stim_gbar=40.0, stim_t0=0.0, stim_t1=1e-3, stim_xmax=0.4 * L, refine=(4, 1))
     raise ValueError(i)
 
 
@@ -151,7 +159,7 @@ def model_a(dim: int, nx: int, dt: float) -> Config:
                   stim_a=p["stim_a"], stim_tau=p["stim_tau"])
 
 
-CONFIGS = {i: (lambda i=i: make_config(i)) for i in range(1, 8)}
+CONFIGS = {i: (lambda i=i: make_config(i)) for i in range(1, 9)}
 
 
 def probe_points(cfg: Config, n: int = 64, seed: int = 2) -> np.ndarray:

@@ -26,23 +26,25 @@ class StructuredMesh:
     length: float           # side of the domain in metres
 
 
-def _vid(idx, n1, dim):
+def _vid(idx, n1s):
     v = idx[..., 0].astype(np.int64)
-    stride = n1
-    for a in range(1, dim):
+    stride = n1s[0]
+    for a in range(1, len(n1s)):
         v = v + idx[..., a].astype(np.int64) * stride
-        stride *= n1
+        stride *= n1s[a]
     return v
 
 
-def structured_mesh(dim: int, nx: int, length: float):
-    """Vertices and simplices of the uniform grid of [0, length]^dim."""
-    n1 = nx + 1
-    axes = [np.arange(n1, dtype=np.float64) / nx * length] * dim
+def structured_mesh(dim: int, nx: int, length: float, axes=None):
+    """Vertices and simplices of the grid of [0, length]^dim: uniform with nx intervals per side,
+    or with the grid-plane coordinates ``axes[a]`` (increasing, from 0 to length) along axis a."""
+    if axes is None:
+        axes = [np.arange(nx + 1, dtype=np.float64) / nx * length] * dim
+    n1s = [len(ax) for ax in axes]
     grid = np.meshgrid(*axes, indexing="ij")
     # lexicographic with x fastest
     coords = np.stack([g.transpose(tuple(range(dim))[::-1]).reshape(-1) for g in grid], axis=1)
-    base = np.stack(np.meshgrid(*[np.arange(nx)] * dim, indexing="ij"), axis=-1)
+    base = np.stack(np.meshgrid(*[np.arange(n - 1) for n in n1s], indexing="ij"), axis=-1)
     base = base.transpose(tuple(range(dim))[::-1] + (dim,)).reshape(-1, dim)
     elems = []
     for perm in itertools.permutations(range(dim)):
@@ -54,10 +56,25 @@ def structured_mesh(dim: int, nx: int, length: float):
             cur = cur.copy()
             cur[:, ax] += 1
             path.append(cur)
-        elems.append(np.stack([_vid(p, n1, dim) for p in path], axis=1))
+        elems.append(np.stack([_vid(p, n1s) for p in path], axis=1))
     # interleave so that the simplices of one grid box are consecutive
     elems = np.stack(elems, axis=1).reshape(-1, dim + 1).astype(np.int32)
     return coords, elems
+
+
+def interface_refined_axis(nx: int, length: float, faces, ratio: int, width: int):
+    """Grid planes of one axis: the uniform grid of nx intervals with every interval within
+    ``width`` intervals of a face plane (uniform grid index) cut into ``ratio`` equal pieces.
+    Returns the plane coordinates and the new index of each uniform plane."""
+    faces = np.unique(np.asarray(faces))
+    pts, new_index = [0.0], [0]
+    for i in range(nx):
+        near = np.any(np.abs(i + 0.5 - faces) <= width)
+        k = ratio if near else 1
+        for j in range(1, k + 1):
+            pts.append((i + j / k) / nx * length)
+        new_index.append(len(pts) - 1)
+    return np.array(pts), np.array(new_index)
 
 
 def snap_boxes(lo: np.ndarray, hi: np.ndarray, nx: int) -> np.ndarray:
@@ -88,25 +105,43 @@ def box_cells(n_per_side: int, side: float, gap: float, dim: int, jitter=None, r
     return np.array(lows), np.array(highs)
 
 
-def tag_grid_boxes(dim: int, nx: int, boxes: np.ndarray) -> np.ndarray:
-    """Tag of every grid box (flattened with x fastest): the last snapped cell box [lo, hi]
-    (grid units) that contains it, 0 if none. A simplex lies in one grid box, and its centroid
-    is strictly inside a snapped cell box exactly when its grid box is, so this is the tag of
-    every simplex of that grid box."""
-    tag = np.zeros((nx,) * dim, dtype=np.int32)          # axes (z, y, x) / (y, x)
+def tag_grid_boxes(dim: int, counts, boxes: np.ndarray) -> np.ndarray:
+    """Tag of every grid box (flattened with x fastest): the last cell box [lo, hi] (grid plane
+    indices) that contains it, 0 if none. ``counts`` is the number of grid boxes along each axis
+    (an int for all). A simplex lies in one grid box, and its centroid is strictly inside a
+    cell box exactly when its grid box is, so this is the tag of every simplex of that grid box."""
+    counts = (counts,) * dim if np.isscalar(counts) else tuple(counts)
+    tag = np.zeros(counts[::-1], dtype=np.int32)          # axes (z, y, x) / (y, x)
     for j, (lo, hi) in enumerate(boxes):
         tag[tuple(slice(int(lo[a]), int(hi[a])) for a in range(dim)[::-1])] = j + 1
     return tag.reshape(-1)
 
 
-def make_mesh(dim: int, nx: int, length: float, lo, hi) -> StructuredMesh:
-    coords, elems = structured_mesh(dim, nx, length)
+def make_mesh(dim: int, nx: int, length: float, lo, hi, refine=None) -> StructuredMesh:
+    """Mesh with box cells snapped to the uniform nx grid. With ``refine`` = (ratio, width), the
+    grid intervals within ``width`` intervals of a cell face plane are cut into ``ratio`` slabs
+    (interface refinement on a tensor grid; the cells do not move). ``boxes`` stay in uniform
+    grid units."""
     boxes = snap_boxes(np.atleast_2d(lo), np.atleast_2d(hi), nx)
     if np.any(boxes[:, 1] - boxes[:, 0] < 1):
         raise ValueError("a cell snapped to zero width")
     if np.any(boxes[:, 0] < 1) or np.any(boxes[:, 1] > nx - 1):
         raise ValueError("cells must stay inside the domain interior")
+    if refine is None:
+        coords, elems = structured_mesh(dim, nx, length)
+        counts, rboxes = (nx,) * dim, boxes
+    else:
+        ratio, width = refine
+        axes, maps = [], []
+        for a in range(dim):
+            ax, mp = interface_refined_axis(nx, length, boxes[:, :, a], ratio, width)
+            axes.append(ax)
+            maps.append(mp)
+        coords, elems = structured_mesh(dim, nx, length, axes)
+        counts = tuple(len(ax) - 1 for ax in axes)
+        rboxes = np.stack([np.stack([maps[a][boxes[:, e, a]] for a in range(dim)], axis=1) for e in range(2)],
+                          axis=1)
     # structured_mesh emits the simplices of one grid box consecutively, grid boxes x fastest
-    per_box = elems.shape[0] // nx ** dim
-    tag = np.repeat(tag_grid_boxes(dim, nx, boxes), per_box)
+    per_box = elems.shape[0] // int(np.prod(counts))
+    tag = np.repeat(tag_grid_boxes(dim, counts, rboxes), per_box)
     return StructuredMesh(dim, nx, coords, elems, tag, boxes, length)

@@ -34,6 +34,8 @@ def _cfgs():
         # Kir-Na/K membrane with the extracellular K bolus (on for 0 < t_n <= 2 ms)
         "kir-2d-32": make_config(7),
         "kir-3d-16": make_config(6).with_nx(16),
+        # interface-refined tensor grid: 16^3 with the intervals next to the cell faces cut in 4
+        "iref-3d-16": make_config(8).with_nx(16),
     }
 
 
@@ -60,7 +62,7 @@ def test_assembly_and_operator(name):
 
 
 STEP_CASES = [("cfg1-2d-leak", 10, "direct"), ("cfg2-3d-hh-16", 8, "lu_p0"), ("cfg4-2d-16cells-32", 5, "direct"),
-              ("kir-2d-32", 24, "direct"), ("kir-3d-16", 6, "lu_p0")]
+              ("kir-2d-32", 24, "direct"), ("kir-3d-16", 6, "lu_p0"), ("iref-3d-16", 5, "lu_p0")]
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64-amg", "fp32-amg"])

@@ -108,3 +108,25 @@ def test_bench_kernel_source_hash():
     bench = importlib.import_module("bench")
     h = bench.kernel_source_hash()
     assert isinstance(h, str) and len(h) == 16
+
+
+def test_interface_refined_grid():
+    """The interface-refined tensor grid: intervals next to the cell faces are cut into `ratio`
+    slabs, the others keep the uniform spacing, the cells keep their snapped extent, and the
+    simplices still tile the domain (volumes add up; the topology builds)."""
+    from synth.mesh import make_mesh
+    nx, L = 16, 1.0
+    m = make_mesh(3, nx, L, np.array([[0.3] * 3]), np.array([[0.7] * 3]), refine=(3, 1))
+    xs = np.unique(m.coords[:, 0])
+    h = np.diff(xs) * nx / L
+    assert np.allclose(np.sort(np.unique(np.round(h, 12))), [1 / 3, 1.0])
+    lo, hi = m.boxes[0, 0], m.boxes[0, 1]                    # snapped to 5 and 11
+    assert (lo[0], hi[0]) == (5, 11)
+    # refined intervals: 4, 5 and 10, 11 (next to the planes 5 and 11)
+    assert len(xs) == nx + 1 + 4 * 2
+    P = m.coords[m.elems]
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6
+    assert abs(vol.sum() - L ** 3) < 1e-12
+    assert abs(vol[m.elem_tag == 1].sum() - ((hi[0] - lo[0]) / nx * L) ** 3) < 1e-12
+    t = build_topology(m.coords, m.elems, m.elem_tag)
+    assert t.N_i > 0 and len(t.facets) == 6 * 2 * (3 * 2 + 4) ** 2
