@@ -45,10 +45,10 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7, 8],
                     help="workload: 2 (default, the headline), 1 (2D leak), 3 (125-cell 3D, FP32 hierarchy, "
                          "rtol 1e-8), 4 (16-cell 2D), 5 (512-cell 256^3, FP32 hierarchy, rtol 1e-8), "
-                         "6 (Kir-Na/K 64^3 with a K bolus), 7 (Kir-Na/K 2D)")
+                         "6 (Kir-Na/K 64^3 with a K bolus), 7 (Kir-Na/K 2D), 8 (3D HH, interface-refined grid)")
     ap.add_argument("--nx", type=int, default=None, help="override the mesh resolution of the workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time a checkpointed forward + adjoint run of the 16-cell 2D workload (KNPFunction)")
@@ -247,6 +247,11 @@ def slowest_rank_ms(ms, world, device):
     t = torch.tensor([ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def device_memory_gb(torch):
+    free, total = torch.cuda.mem_get_info()
+    return (total - free) / 1e9
 
 
 def host_peak_rss_gb():
@@ -452,16 +457,21 @@ def adjoint_bench(args):
     from paper_2403_04491_gb300 import KNPFunction, Simulation, problem_from_config, probe_weights
     from synth import make_config
     from synth.configs import probe_points
-    cfg = make_config(4)
+    # the differentiation workload (4) by default; --config 5 takes the 512-cell 73M-DOF workload
+    # (FP32 hierarchy, rtol 1e-8 unless given), whose run asks for one adjoint step (--steps 1)
+    cfg = make_config(args.config if "--config" in sys.argv and args.config in (4, 5) else 4)
     if args.nx:
         cfg = cfg.with_nx(args.nx)
     n_steps = args.steps if "--steps" in sys.argv else cfg.n_steps
+    rtol = args.rtol if "--rtol" in sys.argv else cfg.rtol
+    t0 = time.perf_counter()
     mesh, prob = problem_from_config(cfg)
-    prob.amg_setup()
+    prob.amg_setup(precision=1 if cfg.mixed else 0)
+    t_setup = time.perf_counter() - t0
     m = cfg.mesh
     ni, ne = mesh.nodes()
     idx, w = probe_weights(m.coords, m.elems, m.elem_tag, ne, prob.N_i, prob.N_e, probe_points(cfg))
-    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=args.rtol)
+    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=rtol)
     gK = torch.tensor(prob._facet_gleak[:, 1].copy(), requires_grad=True)
     cK = torch.tensor(sim.s0["c_i"][1].copy(), requires_grad=True)
     torch.cuda.synchronize()
@@ -475,7 +485,9 @@ def adjoint_bench(args):
     t2 = time.perf_counter()
     line = dict(metric="DOF*timesteps/s, forward and checkpointed adjoint", unit="DOF*steps/s", impl="ours",
                 config=dict(workload=workload_name(cfg, prob.n_dof) + f", {n_steps} steps, checkpoint every 20, "
-                            "loss = sum of phi_e^2 at 64 probes", n_dof=prob.n_dof, rtol=args.rtol),
+                            "loss = sum of phi_e^2 at 64 probes", n_dof=prob.n_dof, rtol=rtol,
+                            precision="fp32" if cfg.mixed else "fp64"),
+                setup_s=t_setup, device_memory_gb=device_memory_gb(torch), host_peak_rss_gb=host_peak_rss_gb(),
                 forward=dict(seconds=t1 - t0, value=prob.n_dof * n_steps / (t1 - t0)),
                 adjoint=dict(seconds=t2 - t1, value=prob.n_dof * n_steps / (t2 - t1),
                              note="includes recomputing every segment from its checkpoint"),

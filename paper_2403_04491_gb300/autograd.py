@@ -17,17 +17,30 @@ from .knp import Problem
 
 def probe_weights(mesh_coords, elems, tag, nodes_e, N_i, N_e, points):
     """P1 interpolation of phi_e at points inside the extracellular mesh: (index [n_p, d+1]
-    into the Eq. 4.3 unknown vector, weight [n_p, d+1])."""
+    into the Eq. 4.3 unknown vector, weight [n_p, d+1]). Each point takes the first extracellular
+    element (in element order) that contains it; elements are screened by the distance of their
+    centroid, which is at most the largest element diameter from any point of the element."""
     ecell = np.nonzero(tag == 0)[0]
-    E = elems[ecell]
-    x = mesh_coords[E]
     d = mesh_coords.shape[1]
     loc = np.full(mesh_coords.shape[0], -1, np.int64)
     loc[nodes_e] = np.arange(len(nodes_e))
-    J = np.linalg.inv((x[:, 1:, :] - x[:, :1, :]).transpose(0, 2, 1))
+    cen = np.empty((len(ecell), d))
+    diam = 0.0
+    chunk = 1 << 22
+    for a in range(0, len(ecell), chunk):
+        x = mesh_coords[elems[ecell[a:a + chunk]]]                  # [m, d+1, d]
+        cen[a:a + chunk] = x.mean(axis=1)
+        diam = max(diam, float(np.sqrt(((x[:, 1:, :] - x[:, :1, :]) ** 2).sum(-1)).max()))
+        for j in range(1, d + 1):
+            for k in range(j + 1, d + 1):
+                diam = max(diam, float(np.sqrt(((x[:, k, :] - x[:, j, :]) ** 2).sum(-1)).max()))
     idx = np.empty((len(points), d + 1), np.int64)
     wts = np.empty((len(points), d + 1))
     for p, pt in enumerate(points):
+        cand = np.flatnonzero(((cen - pt) ** 2).sum(1) <= (diam * (1 + 1e-12)) ** 2)
+        E = elems[ecell[cand]]
+        x = mesh_coords[E]
+        J = np.linalg.inv((x[:, 1:, :] - x[:, :1, :]).transpose(0, 2, 1))
         lam = np.einsum("nij,nj->ni", J, pt - x[:, 0, :])
         bary = np.concatenate([1 - lam.sum(1, keepdims=True), lam], axis=1)
         k = np.flatnonzero(np.all(bary >= -1e-12, axis=1))
