@@ -471,7 +471,7 @@ def adjoint_bench(args):
     m = cfg.mesh
     ni, ne = mesh.nodes()
     idx, w = probe_weights(m.coords, m.elems, m.elem_tag, ne, prob.N_i, prob.N_e, probe_points(cfg))
-    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=rtol)
+    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=rtol, max_it=4000 if cfg.mixed else 1000)
     gK = torch.tensor(prob._facet_gleak[:, 1].copy(), requires_grad=True)
     cK = torch.tensor(sim.s0["c_i"][1].copy(), requires_grad=True)
     torch.cuda.synchronize()
@@ -491,7 +491,10 @@ def adjoint_bench(args):
                 forward=dict(seconds=t1 - t0, value=prob.n_dof * n_steps / (t1 - t0)),
                 adjoint=dict(seconds=t2 - t1, value=prob.n_dof * n_steps / (t2 - t1),
                              note="includes recomputing every segment from its checkpoint"),
-                loss=float(loss), grad_gK_norm=float(gK.grad.norm()), grad_cK_norm=float(cK.grad.norm()))
+                loss=float(loss.detach()), grad_gK_norm=float(gK.grad.norm()), grad_cK_norm=float(cK.grad.norm()),
+                iters_forward=sim.its_forward[:5] + (["..."] if len(sim.its_forward) > 5 else []),
+                iters_adjoint=sim.its_adjoint[:5] + (["..."] if len(sim.its_adjoint) > 5 else []),
+                mean_iters_forward=float(np.mean(sim.its_forward)), mean_iters_adjoint=float(np.mean(sim.its_adjoint)))
     print(json.dumps(line), flush=True)
 
 
