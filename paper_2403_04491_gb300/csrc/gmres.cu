@@ -21,7 +21,10 @@
 // scheduled once that ratio times the current Givens residual |g_k| comes near the threshold.
 // (Apart, because the scaled concentrations outweigh the scaled potentials by two orders.)
 // The host sees one Hessenberg column per iteration.
+#include <algorithm>
 #include <chrono>
+#include <mutex>
+#include <unordered_map>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -34,7 +37,7 @@ namespace knp {
 
 namespace {
 
-constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs: the most blocks a reduction kernel launches
 constexpr int RED_THREADS = 256;
 constexpr int MAXV = 32;          // restart + 2
 constexpr int MAXW = 3 * MAXV;    // partial-sum slots per block
@@ -274,20 +277,50 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_x(int64_t n4, const doub
     }
 }
 
+// Blocks of a grid-stride reduction kernel: one full wave, i.e. the blocks that are resident at
+// once given this kernel's registers (from the occupancy calculator), at most RED_BLOCKS. A fixed
+// grid that is not a multiple of the resident blocks leaves a partly filled last wave that costs
+// as much as a full one (3 resident blocks per SM and 608 blocks ran these kernels 2x slower).
+int red_grid(const void* fn) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(fn);
+    if (it != cache.end()) return it->second;
+    int dev = 0, sms = 0, per_sm = 0;
+    KNP_CUDA(cudaGetDevice(&dev));
+    KNP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    KNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RED_THREADS, 0));
+    const int g = std::max(1, std::min(RED_BLOCKS, per_sm * sms));
+    cache.emplace(fn, g);
+    return g;
+}
+
 #define KNP_NV_CASES(X) \
     X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
     X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
 
-#define KNP_NV_CASE_k_mdot(N) case N: k_mdot<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_mdot_split2(N) case N: k_mdot_split<N, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_mdot_split3(N) case N: k_mdot_split<N, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_combo_norms2(N) case N: k_combo_norms<N, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_combo_norms3(N) case N: k_combo_norms<N, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_orth_update_dot(N) \
-    case N: k_orth_update_dot<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_orth_final(N) case N: k_orth_final<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-#define KNP_NV_CASE_k_update_x(N) case N: k_update_x<N><<<RED_BLOCKS, RED_THREADS, 0, st>>>(KNP_ARGS); break;
-// Launch KERNEL<nv><<<RED_BLOCKS, RED_THREADS, 0, st>>>(args) for a runtime nv in [0, 31]
+#define KNP_NV_CASE_k_mdot(N) \
+    case N: nb_red = red_grid((const void*)&k_mdot<N>); k_mdot<N><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_mdot_split2(N) \
+    case N: nb_red = red_grid((const void*)&k_mdot_split<N, 2>); k_mdot_split<N, 2><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_mdot_split3(N) \
+    case N: nb_red = red_grid((const void*)&k_mdot_split<N, 3>); k_mdot_split<N, 3><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_combo_norms2(N) \
+    case N: nb_red = red_grid((const void*)&k_combo_norms<N, 2>); k_combo_norms<N, 2><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_combo_norms3(N) \
+    case N: nb_red = red_grid((const void*)&k_combo_norms<N, 3>); k_combo_norms<N, 3><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_orth_update_dot(N)                                                        \
+    case N:                                                                                     \
+        nb_red = red_grid((const void*)&k_orth_update_dot<N>);                                  \
+        k_orth_update_dot<N><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS);                         \
+        break;
+#define KNP_NV_CASE_k_orth_final(N) \
+    case N: nb_red = red_grid((const void*)&k_orth_final<N>); k_orth_final<N><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+#define KNP_NV_CASE_k_update_x(N) \
+    case N: nb_red = red_grid((const void*)&k_update_x<N>); k_update_x<N><<<nb_red, RED_THREADS, 0, st>>>(KNP_ARGS); break;
+// Launch KERNEL<nv><<<nb_red, RED_THREADS, 0, st>>>(args) for a runtime nv in [0, 31]; nb_red
+// (a variable of the caller) receives the grid, which the following k_reduce sums over
 #define KNP_LAUNCH_NV(nv, KERNEL)                                                                    \
     do {                                                                                             \
         switch (nv) {                                                                                \
@@ -346,8 +379,9 @@ void gmres_free(GmresWork* g) { delete g; }
 // squared norm of a device vector (through the multi-dot kernels)
 static double norm2_dev(GmresWork& g, const double* v, cudaStream_t st) {
     count_launch(2);
-    k_mdot<0><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g.n4, nullptr, 0, v, g.partial.p);
-    k_reduce<<<1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 1, g.dots.p);
+    const int nb = red_grid((const void*)&k_mdot<0>);
+    k_mdot<0><<<nb, RED_THREADS, 0, st>>>(g.n4, nullptr, 0, v, g.partial.p);
+    k_reduce<<<1, 256, 0, st>>>(g.partial.p, nb, 1, g.dots.p);
     double s;
     KNP_CUDA(cudaMemcpyAsync(&s, g.dots.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     KNP_CUDA(cudaStreamSynchronize(st));
@@ -367,16 +401,21 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     const unsigned nb = (unsigned)((n4 + 255) / 256);
     const int NG = o.phi_e_group ? 3 : 2;
     const int64_t n4i = 4 * p->N_i;
+    int nb_red = RED_BLOCKS;   // grid of the last reduction kernel (KNP_LAUNCH_NV sets it)
     // reference norms of the stopping test, per group: ||S x|| of the iterate a cycle starts from
     // (the initial guess, then each restart's), taken together with the cycle's correction
     double tol[3] = {0, 0, 0};
     auto reference_norms = [&]() {
         count_launch(2);
-        if (NG == 3)
-            k_mdot_split<0, 3><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
-        else
-            k_mdot_split<0, 2><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
-        k_reduce<<<NG, 256, 0, st>>>(g.partial.p, RED_BLOCKS, NG, g.dots.p + 2 * MAXV);
+        int nb = 0;
+        if (NG == 3) {
+            nb = red_grid((const void*)&k_mdot_split<0, 3>);
+            k_mdot_split<0, 3><<<nb, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
+        } else {
+            nb = red_grid((const void*)&k_mdot_split<0, 2>);
+            k_mdot_split<0, 2><<<nb, RED_THREADS, 0, st>>>(n4, nullptr, 0, x, p->swt.p, n4i, g.partial.p);
+        }
+        k_reduce<<<NG, 256, 0, st>>>(g.partial.p, nb, NG, g.dots.p + 2 * MAXV);
         double xn2[3] = {0, 0, 0};
         KNP_CUDA(cudaMemcpyAsync(xn2, g.dots.p + 2 * MAXV, NG * sizeof(double), cudaMemcpyDeviceToHost, st));
         KNP_CUDA(cudaStreamSynchronize(st));
@@ -466,7 +505,7 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                 else
                     KNP_LAUNCH_NV(j + 1, k_combo_norms2);
 #undef KNP_ARGS
-                k_reduce<<<2 * NG, 256, 0, st>>>(g.partial.p, RED_BLOCKS, 2 * NG, g.dots.p + CHK_OFF);
+                k_reduce<<<2 * NG, 256, 0, st>>>(g.partial.p, nb_red, 2 * NG, g.dots.p + CHK_OFF);
             }
             int nv = j + 1;
             if (arnoldi) {
@@ -477,11 +516,11 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
 #define KNP_ARGS n4, g.V.p, n4, w, g.partial.p
                 KNP_LAUNCH_NV(nv, k_mdot);
 #undef KNP_ARGS
-                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p);
+                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, nb_red, nv + 1, g.dots.p);
 #define KNP_ARGS n4, g.V.p, n4, g.dots.p, w, g.partial.p
                 KNP_LAUNCH_NV(nv, k_orth_update_dot);
 #undef KNP_ARGS
-                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, RED_BLOCKS, nv + 1, g.dots.p + MAXV);
+                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, nb_red, nv + 1, g.dots.p + MAXV);
 #define KNP_ARGS n4, g.V.p, n4, g.dots.p + MAXV, w, g.dots.p + 2 * MAXV + MAXW
                 KNP_LAUNCH_NV(nv, k_orth_final);
 #undef KNP_ARGS
