@@ -148,6 +148,10 @@ typedef struct {
 knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc, void* stream,
                               knp_problem** out);
 void knp_problem_destroy(knp_problem* prob);
+/* Waits for all work the library has enqueued for this problem on its stream (the library's
+ * calls are stream-ordered; knp_solve, knp_step and the getters that return host data
+ * synchronise by themselves). Errors: KNP_ERR_INVALID_ARG, KNP_ERR_CUDA (the stream's error). */
+knp_status knp_sync(knp_problem* prob);
 
 /* Membrane update and assembly for the current step n (Section 3.2, Section
  * 4.1): from u_{n-1}, w_{n-1} and t_{n-1}, computes w_n by Rush-Larsen with

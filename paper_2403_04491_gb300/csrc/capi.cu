@@ -147,6 +147,13 @@ void knp_problem_destroy(knp_problem* p) {
     delete p;
 }
 
+knp_status knp_sync(knp_problem* p) {
+    return guarded([&] {
+        KNP_REQUIRE(p, KNP_ERR_INVALID_ARG, "NULL problem");
+        KNP_CUDA(cudaStreamSynchronize(p->stream));
+    });
+}
+
 knp_status knp_assemble_step(knp_problem* p) {
     return guarded([&] {
         KNP_REQUIRE(p, KNP_ERR_INVALID_ARG, "NULL problem");

@@ -96,6 +96,7 @@ SIGNATURES = {
     "knp_mesh_destroy": [C.c_void_p],
     "knp_problem_create": [C.c_void_p, C.POINTER(ProblemDesc), C.c_void_p, C.POINTER(C.c_void_p)],
     "knp_problem_destroy": [C.c_void_p],
+    "knp_sync": [C.c_void_p],
     "knp_assemble_step": [C.c_void_p],
     "knp_amg_setup": [C.c_void_p, C.POINTER(AmgOpts)],
     "knp_solve": [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveStats)],
@@ -272,6 +273,10 @@ class Problem:
         self.N_i, self.N_e = mesh.info["N_i"], mesh.info["N_e"]
         self.n_mv = mesh.info["n_membrane_vertices"]
         self.n_dof = 4 * (self.N_i + self.N_e)
+
+    def sync(self):
+        """Wait for the work enqueued for this problem on its stream."""
+        _check(_lib.knp_sync(self.handle))
 
     # -- per step
     def assemble_step(self):

@@ -132,6 +132,8 @@ def test_state_roundtrip_and_resume():
     cfg = make_config(2).with_nx(12)
     _, a = problem_from_config(cfg)
     a.amg_setup()
+    a.assemble_step()          # stream-ordered, returns at once; knp_sync waits for it
+    a.sync()
     a.step(2, rtol=1e-10)
     saved = a.state_get()
     a.step(2, rtol=1e-10)
