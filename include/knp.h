@@ -66,6 +66,8 @@ typedef struct {
     int64_t n_elems;
     const int32_t* elems;      /* host [n_elems * (dim+1)] vertex ids */
     const int32_t* elem_tag;   /* host [n_elems]: 0 = extracellular, j >= 1 = cell j */
+    const double* pin_point;   /* host [dim] or NULL (= the origin): the phi_e pin of Remark 4.1 goes on
+                                  the extracellular vertex nearest to this point, ties by lowest id */
 } knp_mesh_desc;
 
 typedef struct {

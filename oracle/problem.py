@@ -20,10 +20,10 @@ def facet_inputs(cfg, topo, coords):
     return model, gleak, mask
 
 
-def from_config(cfg, dt=None):
+def from_config(cfg, dt=None, pin_point=None):
     m = cfg.mesh
     p = cfg.params
-    topo = build_topology(m.coords, m.elems, m.elem_tag)
+    topo = build_topology(m.coords, m.elems, m.elem_tag, pin_point=pin_point)
     model, gleak, mask = facet_inputs(cfg, topo, m.coords)
     pb = system.Problem(topo=topo, coords=m.coords, elems=m.elems, R=p["R"], T=p["T"], F=p["F"],
                         Cm=p["Cm"], z=np.asarray(p["z"], float), D_i=np.asarray(p["D"], float),

@@ -50,7 +50,7 @@ class InvalidMesh(ValueError):
     pass
 
 
-def build_topology(coords: np.ndarray, elems: np.ndarray, tag: np.ndarray) -> Topology:
+def build_topology(coords: np.ndarray, elems: np.ndarray, tag: np.ndarray, pin_point=None) -> Topology:
     n_v, dim = coords.shape
     n_e = elems.shape[0]
     # all (element, local facet) pairs; facet s is opposite local vertex s
@@ -113,8 +113,10 @@ def build_topology(coords: np.ndarray, elems: np.ndarray, tag: np.ndarray) -> To
     if not np.all(np.isin(cells_present, facet_cell)):
         raise InvalidMesh("a cell has no membrane facet")
 
-    # pin: extracellular vertex nearest to the origin corner, ties by lowest id
-    d2 = np.sum(coords[nodes_e] ** 2, axis=1)
+    # pin: extracellular vertex nearest to the pin point (the origin corner by default), ties by
+    # lowest id (Remark 4.1 allows any extracellular node)
+    p0 = np.zeros(coords.shape[1]) if pin_point is None else np.asarray(pin_point, float)
+    d2 = np.sum((coords[nodes_e] - p0) ** 2, axis=1)
     k = np.flatnonzero(d2 == d2.min())[0]
     return Topology(dim, n_v, nodes_i, nodes_e, loc_i, loc_e, elems_i, elems_e, facets,
                     facet_cell, facet_elem_i, facet_opp_i, np.nonzero(on_gamma)[0],

@@ -65,6 +65,7 @@ struct knp_mesh {
     std::vector<int32_t> mverts;             // membrane vertices, increasing
     std::vector<int32_t> node_cell_i;        // cell tag of each intracellular node
     int64_t pin_vertex = -1;
+    double pin_point[3] = {0.0, 0.0, 0.0};   // the pin goes on the e-vertex nearest to this point
     int32_t n_cells = 0;
     int64_t nf() const { return (int64_t)facet_cell.size(); }
 };

@@ -148,11 +148,14 @@ void build_topology(knp_mesh& m) {
         }
         if (on_g[v]) m.mverts.push_back((int32_t)v);
     }
-    // pin: extracellular vertex nearest to the origin, ties by lowest id
+    // pin: extracellular vertex nearest to the pin point (the origin by default), ties by lowest id
     double best = INFINITY;
     for (int32_t v : m.nodes_e) {
         double d2 = 0;
-        for (int d = 0; d < dim; ++d) d2 += m.coords[(int64_t)v * dim + d] * m.coords[(int64_t)v * dim + d];
+        for (int d = 0; d < dim; ++d) {
+            const double x = m.coords[(int64_t)v * dim + d] - m.pin_point[d];
+            d2 += x * x;
+        }
         if (d2 < best) {
             best = d2;
             m.pin_vertex = v;
@@ -185,6 +188,11 @@ knp_status knp_mesh_create(const knp_mesh_desc* d, knp_mesh** out) {
             m->coords.assign(d->coords, d->coords + d->n_vertices * d->dim);
             m->elems.assign(d->elems, d->elems + d->n_elems * (d->dim + 1));
             m->tag.assign(d->elem_tag, d->elem_tag + d->n_elems);
+            if (d->pin_point)
+                for (int k = 0; k < d->dim; ++k) {
+                    KNP_REQUIRE(std::isfinite(d->pin_point[k]), KNP_ERR_INVALID_ARG, "pin point is not finite");
+                    m->pin_point[k] = d->pin_point[k];
+                }
             build_topology(*m);
         } catch (...) {
             delete m;

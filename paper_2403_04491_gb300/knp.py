@@ -32,7 +32,8 @@ class KnpError(RuntimeError):
 
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("coords", C.POINTER(C.c_double)),
-                ("n_elems", C.c_int64), ("elems", C.POINTER(C.c_int32)), ("elem_tag", C.POINTER(C.c_int32))]
+                ("n_elems", C.c_int64), ("elems", C.POINTER(C.c_int32)), ("elem_tag", C.POINTER(C.c_int32)),
+                ("pin_point", C.POINTER(C.c_double))]
 
 
 class MeshInfo(C.Structure):
@@ -164,13 +165,15 @@ def _lptr(a):
 class Mesh:
     """knp_mesh_create: conforming simplicial mesh with cell tags (0 = extracellular)."""
 
-    def __init__(self, coords, elems, tag):
+    def __init__(self, coords, elems, tag, pin_point=None):
+        """pin_point: the phi_e pin goes on the extracellular vertex nearest to it (default: origin)."""
         lib = load_library()
         self._coords = np.ascontiguousarray(coords, dtype=np.float64)
         self._elems = np.ascontiguousarray(elems, dtype=np.int32)
         self._tag = np.ascontiguousarray(tag, dtype=np.int32)
+        self._pin = None if pin_point is None else np.ascontiguousarray(pin_point, dtype=np.float64)
         d = MeshDesc(self._coords.shape[1], self._coords.shape[0], _dptr(self._coords), self._elems.shape[0],
-                     _iptr(self._elems), _iptr(self._tag))
+                     _iptr(self._elems), _iptr(self._tag), None if self._pin is None else _dptr(self._pin))
         h = C.c_void_p()
         _check(lib.knp_mesh_create(C.byref(d), C.byref(h)))
         self.handle = h

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from helpers import (blockscaled_entry_error, blockwise_vector_error, oracle_run, rel_errors)
-from oracle import problem as oproblem, system as osystem
+from oracle import problem as oproblem, step as ostep, system as osystem
 from synth import make_config
 
 pytestmark = pytest.mark.gpu
@@ -216,3 +216,24 @@ def test_cg_p0_inner_solve():
             assert ec <= TOL and ep <= TOL, (inner, n, ec, ep)
     print("FGMRES iterations, AMG(P_0):", its[0], "CG(P_0):", its[60])
     assert sum(its[60]) <= sum(its[0])
+
+
+def test_pin_point_far_corner():
+    """The phi_e pin placed at the extracellular vertex nearest to the far corner (L, L) instead of
+    the origin: the steps match the oracle with the same pin."""
+    from paper_2403_04491_gb300 import Mesh, problem_from_config
+    cfg = make_config(1)
+    pt = np.array([cfg.length, cfg.length])
+    pb, s0 = oproblem.from_config(cfg, pin_point=pt)
+    ref = [s0]
+    for _ in range(4):
+        ref.append(ostep.step(pb, ref[-1])[0])
+    m = cfg.mesh
+    mesh = Mesh(m.coords, m.elems, m.elem_tag, pin_point=pt)
+    assert mesh.info["pin_vertex"] == pb.topo.pin_vertex
+    _, prob = problem_from_config(cfg, mesh=mesh)
+    prob.amg_setup()
+    for n in range(1, 5):
+        prob.step(1, rtol=1e-10)
+        ec, ep = rel_errors(prob.state_get(), ref[n])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep)

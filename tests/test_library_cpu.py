@@ -130,3 +130,20 @@ def test_interface_refined_grid():
     assert abs(vol[m.elem_tag == 1].sum() - ((hi[0] - lo[0]) / nx * L) ** 3) < 1e-12
     t = build_topology(m.coords, m.elems, m.elem_tag)
     assert t.N_i > 0 and len(t.facets) == 6 * 2 * (3 * 2 + 4) ** 2
+
+
+@pytest.mark.parametrize("where", [(1.0, 1.0), (0.5, 0.02), (0.24, 0.5)])
+def test_pin_point(lib, where):
+    """The phi_e pin goes on the extracellular vertex nearest to the given point (Remark 4.1 allows
+    any extracellular node), in the library as in the oracle; the default is the origin."""
+    from paper_2403_04491_gb300 import Mesh
+    cfg = make_config(1)
+    m = cfg.mesh
+    pt = np.asarray(where) * cfg.length
+    M = Mesh(m.coords, m.elems, m.elem_tag, pin_point=pt)
+    T = build_topology(m.coords, m.elems, m.elem_tag, pin_point=pt)
+    assert M.info["pin_vertex"] == T.pin_vertex
+    # the nearest extracellular vertex, by brute force
+    d = np.sum((m.coords[T.nodes_e] - pt) ** 2, axis=1)
+    assert T.pin_vertex == T.nodes_e[np.flatnonzero(d == d.min())[0]]
+    assert Mesh(m.coords, m.elems, m.elem_tag).info["pin_vertex"] == build_topology(m.coords, m.elems, m.elem_tag).pin_vertex
