@@ -4,7 +4,7 @@ Unknown order (Eq. 4.3): [c_i^1 .. c_i^|K|, phi_i, c_e^1 .. c_e^|K|, phi_e], eac
 block in region node order. Blocks follow the matrices A_r^n and B_rq^n of
 Section 4.1 with tau_r^k = dt D_r^k and tau~_r^k = tau_r^k z_k / psi, psi = RT/F.
 
-Readings where the paper is silent or inconsistent (also listed in the design doc):
+Readings where the paper is silent or inconsistent:
   * the bulk source enters the right-hand side multiplied by dt (Eq. 3.5 omits it), with
     nodal values, evaluated at t_n (f_r^{k,n} of Section 3.2);
   * Kir-Na/K facets (Section 2.4.2): the rectification factor and the pump flux are nodal, like
