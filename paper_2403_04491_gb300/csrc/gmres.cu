@@ -23,6 +23,7 @@
 // The host sees one Hessenberg column per iteration.
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <mutex>
 #include <unordered_map>
 #include <cmath>
@@ -348,7 +349,13 @@ struct GmresWork {
     DArray<double> V, Z, partial, dots, y, cy, tmp;
     double* hh = nullptr;           // pinned copy of dots, DOTS_LEN
     cudaEvent_t ev_dots = nullptr;  // recorded after the copy of dots to hh
+    // the Arnoldi step of basis index j (SpMV, the three orthogonalisation passes with their
+    // reductions, the copy of the dots to hh) as a CUDA graph per (j, transposed)
+    std::map<std::pair<int, bool>, cudaGraphExec_t> arnoldi;
+    cudaStream_t cap = nullptr;     // capture stream (the problem's stream may be the legacy one)
     ~GmresWork() {
+        for (auto& kv : arnoldi) cudaGraphExecDestroy(kv.second);
+        if (cap) cudaStreamDestroy(cap);
         if (hh) cudaFreeHost(hh);
         if (ev_dots) cudaEventDestroy(ev_dots);
     }
@@ -388,6 +395,62 @@ static double norm2_dev(GmresWork& g, const double* v, cudaStream_t st) {
     return s;
 }
 
+// w = S^-1 A z_j into V_{j+1}, orthogonalised against V_0..V_j (CGS2, second pass skipped on the
+// device when it has nothing to remove) and normalised; the dots of both passes land in g.dots
+static void arnoldi_kernels(knp_problem* p, GmresWork& g, int j, bool transpose, cudaStream_t st) {
+    const int64_t n4 = g.n4;
+    const int nv = j + 1;
+    int nb_red = RED_BLOCKS;
+    double* zj = g.Z.p + (int64_t)j * n4;
+    double* w = g.V.p + (int64_t)(j + 1) * n4;
+    op_apply(p, zj, w, p->sinv.p, nullptr, transpose, st);
+    ProfScope ps(&p->prof, KC_ORTHO, st);
+    count_launch(5);
+#define KNP_ARGS n4, g.V.p, n4, w, g.partial.p
+    KNP_LAUNCH_NV(nv, k_mdot);
+#undef KNP_ARGS
+    k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, nb_red, nv + 1, g.dots.p);
+#define KNP_ARGS n4, g.V.p, n4, g.dots.p, w, g.partial.p
+    KNP_LAUNCH_NV(nv, k_orth_update_dot);
+#undef KNP_ARGS
+    k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, nb_red, nv + 1, g.dots.p + MAXV);
+#define KNP_ARGS n4, g.V.p, n4, g.dots.p + MAXV, w, g.dots.p + 2 * MAXV + MAXW
+    KNP_LAUNCH_NV(nv, k_orth_final);
+#undef KNP_ARGS
+    KNP_CUDA(cudaGetLastError());
+}
+
+// The Arnoldi step j followed by the copy of the dots to the pinned g.hh, replayed from a CUDA
+// graph captured at first use (about ten launches become one).
+static void arnoldi_graph_launch(knp_problem* p, GmresWork& g, int j, bool transpose) {
+    auto key = std::make_pair(j, transpose);
+    auto it = g.arnoldi.find(key);
+    if (it == g.arnoldi.end()) {
+        if (!g.cap) KNP_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+        const int64_t before = g_launches.load();
+        KNP_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            arnoldi_kernels(p, g, j, transpose, g.cap);
+            KNP_CUDA(cudaMemcpyAsync(g.hh, g.dots.p, DOTS_LEN * sizeof(double), cudaMemcpyDeviceToHost, g.cap));
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(g.cap, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            throw;
+        }
+        cudaGraph_t graph = nullptr;
+        KNP_CUDA(cudaStreamEndCapture(g.cap, &graph));
+        g_launches.fetch_sub(g_launches.load() - before);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        KNP_CUDA(e);
+        it = g.arnoldi.emplace(key, ex).first;
+    }
+    KNP_CUDA(cudaGraphLaunch(it->second, p->stream));
+    count_launch(6);
+}
+
 knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stats& stats, double* x,
                          const double* fvec, bool transpose) {
     auto t0 = std::chrono::steady_clock::now();
@@ -402,6 +465,9 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     const int NG = o.phi_e_group ? 3 : 2;
     const int64_t n4i = 4 * p->N_i;
     int nb_red = RED_BLOCKS;   // grid of the last reduction kernel (KNP_LAUNCH_NV sets it)
+    // Arnoldi steps from CUDA graphs, unless a kernel class is being profiled (event pairs go
+    // around single launches) or graphs are switched off for the V-cycle as well
+    const bool use_graphs = p->amg->use_graphs && p->prof.active < 0;
     // reference norms of the stopping test, per group: ||S x|| of the iterate a cycle starts from
     // (the initial guess, then each restart's), taken together with the cycle's correction
     double tol[3] = {0, 0, 0};
@@ -507,25 +573,13 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
 #undef KNP_ARGS
                 k_reduce<<<2 * NG, 256, 0, st>>>(g.partial.p, nb_red, 2 * NG, g.dots.p + CHK_OFF);
             }
-            int nv = j + 1;
-            if (arnoldi) {
-                double* w = g.V.p + (int64_t)(j + 1) * n4;
-                op_apply(p, zj, w, p->sinv.p, nullptr, transpose);
-                ProfScope ps(&p->prof, KC_ORTHO, st);
-                count_launch(5);
-#define KNP_ARGS n4, g.V.p, n4, w, g.partial.p
-                KNP_LAUNCH_NV(nv, k_mdot);
-#undef KNP_ARGS
-                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, nb_red, nv + 1, g.dots.p);
-#define KNP_ARGS n4, g.V.p, n4, g.dots.p, w, g.partial.p
-                KNP_LAUNCH_NV(nv, k_orth_update_dot);
-#undef KNP_ARGS
-                k_reduce<<<nv + 1, 256, 0, st>>>(g.partial.p, nb_red, nv + 1, g.dots.p + MAXV);
-#define KNP_ARGS n4, g.V.p, n4, g.dots.p + MAXV, w, g.dots.p + 2 * MAXV + MAXW
-                KNP_LAUNCH_NV(nv, k_orth_final);
-#undef KNP_ARGS
+            const int nv = j + 1;
+            if (arnoldi && use_graphs) {
+                arnoldi_graph_launch(p, g, j, transpose);   // includes the copy of the dots
+            } else {
+                if (arnoldi) arnoldi_kernels(p, g, j, transpose, st);
+                KNP_CUDA(cudaMemcpyAsync(g.hh, g.dots.p, DOTS_LEN * sizeof(double), cudaMemcpyDeviceToHost, st));
             }
-            KNP_CUDA(cudaMemcpyAsync(g.hh, g.dots.p, DOTS_LEN * sizeof(double), cudaMemcpyDeviceToHost, st));
             KNP_CUDA(cudaEventRecord(g.ev_dots, st));
             if (arnoldi) {
                 // v_{j+1} is already normalised on the device: queue its V-cycle before the host

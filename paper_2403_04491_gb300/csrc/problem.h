@@ -169,7 +169,10 @@ void adjoint_step(knp_problem* P, bool device, const double* u_n, const double* 
 void adjoint_get(knp_problem* P, bool device, double* dLdu0, double* dLdw0, double* grad, double* lambda);
 // spmv.cu
 // y = A x (unscaled), or with row scaling / residual; see spmv.cu
+// stands for "the problem's own stream" in stream arguments
+inline const cudaStream_t kProblemStream = reinterpret_cast<cudaStream_t>(~uintptr_t(0));
+// (on `st`, or on the problem's stream when st is the default argument)
 void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b,
-              bool transpose = false);
+              bool transpose = false, cudaStream_t st = kProblemStream);
 void download_state(const knp_problem* p, std::vector<double>& u);
 }  // namespace knp

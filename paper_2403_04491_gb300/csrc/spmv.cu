@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(128) k_op_apply_t(OpArgs A, const double* __re
 
 }  // namespace
 
-void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b, bool transpose) {
+void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b, bool transpose,
+              cudaStream_t st) {
+    if (st == kProblemStream) st = p->stream;
     OpArgs A;
     A.n = p->n_nodes;
     A.N_i = p->N_i;
@@ -162,12 +164,12 @@ void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale
         for (int k = 0; k < KI; ++k) A.tau[r][k] = p->sp.reg[r].tau[k];
     for (int k = 0; k < KI; ++k) A.z[k] = p->sp.z[k];
     unsigned blocks = (unsigned)((A.n + 127) / 128);
-    ProfScope ps(&p->prof, KC_SPMV, p->stream);
+    ProfScope ps(&p->prof, KC_SPMV, st);
     count_launch();
     if (transpose)
-        k_op_apply_t<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
+        k_op_apply_t<<<blocks, 128, 0, st>>>(A, x, y, rowscale, b);
     else
-        k_op_apply<<<blocks, 128, 0, p->stream>>>(A, x, y, rowscale, b);
+        k_op_apply<<<blocks, 128, 0, st>>>(A, x, y, rowscale, b);
     KNP_CUDA(cudaGetLastError());
 }
 
