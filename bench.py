@@ -177,16 +177,24 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- our arm
 
-def kernel_source_hash():
-    """Hash of the source text of the finest-level Chebyshev step (sell_row, cheb_update,
-    k_cheb_sell), so that DRAM counters taken on an older version of it are not reported."""
-    src = open(os.path.join(ROOT, "paper_2403_04491_gb300", "csrc", "vcycle.cu")).read()
+def _source_parts(path, spans):
+    src = open(os.path.join(ROOT, "paper_2403_04491_gb300", "csrc", path)).read()
     parts = []
-    for start, end in (("// Row product of a sliced-ELL operator", "// Field f of a CSR row product"),
-                       ("// Chebyshev update of one row", "template <class T, int S>\n__global__ void __launch_bounds__(128) k_cheb_csr")):
-        i = src.index(start)
-        parts.append(src[i:src.index(end, i)])
+    for start, end in spans:
+        a = src.index(start)
+        parts.append(src[a:src.index(end, a)])
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
+def kernel_source_hash(kind="cheb_fine"):
+    """Hash of a reported kernel's source text, so that DRAM counters taken on an older version of
+    it are not reported: "cheb_fine" (sell_row, cheb_update, k_cheb_sell) or "spmv" (k_op_apply)."""
+    if kind == "spmv":
+        return _source_parts("spmv.cu", (("__global__ void __launch_bounds__(128) k_op_apply(",
+                                          "// y = rowscale .* (b - A^T x)"),))
+    return _source_parts("vcycle.cu", (("// Row product of a sliced-ELL operator", "// Field f of a CSR row product"),
+                                       ("// Chebyshev update of one row",
+                                        "template <class T, int S>\n__global__ void __launch_bounds__(128) k_cheb_csr")))
 
 
 def fp64_peak_tflops(torch):
@@ -209,13 +217,24 @@ def fp64_peak_tflops(torch):
 
 
 def dominant_kernel_work(prob, precision):
-    """Algorithmic bytes and FLOPs of one finest-level Chebyshev step. Bytes: the operator once
+    """Algorithmic bytes and FLOPs of one finest-level Chebyshev step (the V-cycle's largest kernel). Bytes: the operator once
     (column index + four values per stored entry) and six node vectors of four values (x gathered,
     b, D^-1, d read, d written, x written). FLOPs: 4 FMAs per stored entry and 20 per row."""
     info = prob.amg_info()
     n, nnz = info["nodes"][0], info["nnz"][0]
     t = 8 if precision == "fp64" else 4
     return nnz * (4 + 4 * t) + n * 4 * t * 6, 8.0 * nnz + 20.0 * n
+
+
+def spmv_work(prob):
+    """Algorithmic bytes and FLOPs of one operator SpMV y = S^-1 A x (k_op_apply, the Arnoldi
+    form without a right-hand side). Bytes: per stored same-region entry a column index and five
+    FP64 values (m, a, e^1..e^3), per cross-region entry an index and three values, per node
+    the gathered x, the row scale and y (four FP64 each). FLOPs: 9 FMAs per same-region entry,
+    3 per cross entry, 20 per row."""
+    info = prob.info()
+    n, nnz, nx = info["n_nodes"], info["nnz_region"], info["nnz_cross"]
+    return nnz * (4 + 40) + nx * (4 + 24) + n * 3 * 32, 18.0 * nnz + 6.0 * nx + 20.0 * n
 
 
 def measure(prob, torch, steps, rtol, kernel_class=None):
@@ -312,13 +331,14 @@ def ours(args):
     # same number of steps (event pairs go around single launches, so the V-cycle is not replayed
     # from its CUDA graph in this pass)
     _, _, _, prof = measure(prob, torch, args.steps, args.rtol, kernel_class=1)
+    _, _, _, prof_spmv = measure(prob, torch, args.steps, args.rtol, kernel_class=0)
     ms = slowest_rank_ms(ms, world, "cuda")
 
     # end to end through the public API with host buffers: per step the state goes host->device,
     # one knp_step runs, and the new state comes back device->host (pinned host memory)
     e2e = None if args.no_e2e else e2e_run(prob, torch, args, n_dof, world)
     mixed = None if (args.no_mixed or args.config != 2) else mixed_run(cfg, mesh, torch, args, n_dof)
-    report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg,
+    report(args, prob, world, rank, ms, iters, launches, (prof, prof_spmv), clocks, e2e, mixed, n_dof, t_create, t_amg,
            workload_name(cfg, n_dof), mem_gb)
 
 
@@ -395,34 +415,41 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    n_launch, prof_ms = prof
-    bytes_per, flops_per = dominant_kernel_work(prob, args.precision)
-    avg_s = prof_ms / n_launch / 1e3 if n_launch else None
-    gbs = bytes_per / avg_s / 1e9 if avg_s else None
-    traffic = None
-    if os.path.exists(PROFILE_FILE):
-        pf = json.load(open(PROFILE_FILE))
-        ent = pf.get(f"cheb_fine_{args.precision}")
+    import torch
+    p64 = fp64_peak_tflops(torch)
+    pf = json.load(open(PROFILE_FILE)) if os.path.exists(PROFILE_FILE) else {}
+
+    def roofline(prof_k, work, key, kind, name, fp64_bound):
+        """roofline object of one kernel from its per-launch event timing (n launches, total ms)."""
+        n_launch, prof_ms = prof_k
+        bytes_per, flops_per = work
+        avg_s = prof_ms / n_launch / 1e3 if n_launch else None
+        gbs = bytes_per / avg_s / 1e9 if avg_s else None
+        ent = pf.get(key)
         # counters hold for the kernel text and the workload they were taken on
-        if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("n_dof") == n_dof:
-            traffic = ent.get("dram_bytes_per_launch")
-    hbm = dict(achieved=gbs, peak=peak, unit="GB/s", frac=(gbs / peak) if gbs else None,
-               peak_source="measured" if "hbm_gbs" in peaks else "fallback")
-    common = dict(kernel="k_cheb_sell (finest-level Chebyshev step of the V-cycle)", traffic=traffic,
-                  algorithmic_bytes_per_launch=bytes_per, algorithmic_flops_per_launch=flops_per,
-                  launches=n_launch, avg_launch_us=1e6 * avg_s if avg_s else None,
-                  share_of_step=prof_ms / ms if ms else None)
-    if args.precision == "fp64":
-        # FP64 arithmetic bounds this kernel on GB300 (FP64 pipe ~80% busy at ~47% of HBM, see
-        # profiles/): report against the measured FP64 rate, with the HBM fraction beside it
-        import torch
-        p64 = fp64_peak_tflops(torch)
-        tf = flops_per / avg_s / 1e12 if avg_s else None
-        roof = dict(bound="alu", achieved=tf, peak=p64, unit="TFLOP/s", frac=(tf / p64) if tf else None,
-                    peak_source="measured FP64 DGEMM 4096^3 in this run", hbm=hbm, **common)
-    else:
-        roof = dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=hbm["frac"],
+        traffic = ent.get("dram_bytes_per_launch") if (ent and ent.get("source_hash") == kernel_source_hash(kind)
+                                                       and ent.get("n_dof") == n_dof) else None
+        hbm = dict(achieved=gbs, peak=peak, unit="GB/s", frac=(gbs / peak) if gbs else None,
+                   peak_source="measured" if "hbm_gbs" in peaks else "fallback")
+        common = dict(kernel=name, traffic=traffic, algorithmic_bytes_per_launch=bytes_per,
+                      algorithmic_flops_per_launch=flops_per, launches=n_launch,
+                      avg_launch_us=1e6 * avg_s if avg_s else None, share_of_step=prof_ms / ms if ms else None)
+        if fp64_bound:
+            # FP64 arithmetic bounds these kernels on GB300 (FP64 pipe 70-80% busy at about half
+            # of HBM, see profiles/): report against the measured FP64 rate, HBM fraction beside it
+            tf = flops_per / avg_s / 1e12 if avg_s else None
+            return dict(bound="alu", achieved=tf, peak=p64, unit="TFLOP/s", frac=(tf / p64) if tf else None,
+                        peak_source="measured FP64 DGEMM 4096^3 in this run", hbm=hbm, **common)
+        return dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=hbm["frac"],
                     peak_source=hbm["peak_source"], **common)
+
+    # the dominant kernel: the operator SpMV (FP64 in both forms), the largest single kernel of
+    # the step (profiles/launches_bench_*); beside it the finest Chebyshev step of the V-cycle
+    roof = roofline(prof[1], spmv_work(prob), "spmv_fp64", "spmv",
+                    "k_op_apply (operator SpMV S^-1 A x, FP64)", True)
+    roof_vc = roofline(prof[0], dominant_kernel_work(prob, args.precision), f"cheb_fine_{args.precision}",
+                       "cheb_fine", "k_cheb_sell (finest-level Chebyshev step of the V-cycle)",
+                       args.precision == "fp64")
     if mixed and args.precision == "fp64" and args.rtol == 1e-10:
         # the mixed form at its tolerance (1e-8) against the plain FP64 path at its own (1e-10)
         mixed["speedup_fp32_rtol_1e-08_vs_plain_fp64_rtol_1e-10"] = mixed["rtol_1e-08"]["value"] / value
@@ -440,6 +467,7 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 iters_per_step=float(np.mean(iters)), iters=iters, setup_s=dict(create=t_create, amg=t_amg),
                 amg=prob.amg_info(), gpu_launches=launches, clocks=clocks, roofline=roof,
+                roofline_vcycle=roof_vc,
                 device_memory_gb=mem_gb, host_peak_rss_gb=host_peak_rss_gb(),
                 e2e=e2e, cpu_baseline=cpu, mixed=mixed)
     print(json.dumps(line), flush=True)

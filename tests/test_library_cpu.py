@@ -106,8 +106,9 @@ def test_bench_kernel_source_hash():
     import sys
     sys.path.insert(0, str(ROOT))
     bench = importlib.import_module("bench")
-    h = bench.kernel_source_hash()
-    assert isinstance(h, str) and len(h) == 16
+    for kind in ("cheb_fine", "spmv"):
+        h = bench.kernel_source_hash(kind)
+        assert isinstance(h, str) and len(h) == 16
 
 
 def test_interface_refined_grid():
