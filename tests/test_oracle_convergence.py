@@ -5,7 +5,9 @@ is computed on structured meshes with N = 16, 32, 64, 128 intervals per side, an
 solutions are compared at the coarse mesh's vertices (every coarse vertex is a fine vertex).
 The geometry is a strip cell x in (L/4, 3L/4) across the whole height, so that the membrane has
 no corners (the square cell's corners are re-entrant corners of the extracellular domain, whose
-singularities lower the observed orders). P1 elements give second order for the concentrations;
+singularities lower the observed orders). P1 elements give second order for the concentrations
+and for the potentials up to their constant (the constant itself, fixed by the one-point pin,
+converges more slowly);
 the backward-Euler-type time step gives first order in dt. No manufactured solution, and so no
 second derivation of the equations, is needed."""
 from dataclasses import replace
@@ -59,12 +61,15 @@ def test_second_order_in_space():
         mi, me = _at(pbc, pbf, "i"), _at(pbc, pbf, "e")
         ec.append(np.sqrt(np.mean(np.concatenate([(sc.c_i - sf.c_i[:, mi]).ravel(),
                                                    (sc.c_e - sf.c_e[:, me]).ravel()]) ** 2)))
-        ep.append(np.sqrt(np.mean(np.concatenate([sc.phi_i - sf.phi_i[mi], sc.phi_e - sf.phi_e[me]]) ** 2)))
+        # the potentials are defined up to a constant, which the point pin of Remark 4.1 fixes by
+        # one pointwise value; compare them without that constant (the mean difference of phi_e)
+        di, de = sc.phi_i - sf.phi_i[mi], sc.phi_e - sf.phi_e[me]
+        shift = de.mean()
+        ep.append(np.sqrt(np.mean(np.concatenate([di - shift, de - shift]) ** 2)))
     oc, op = _orders(ec), _orders(ep)
-    print("concentration orders", oc, "potential orders", op)
+    print("concentration orders", oc, "potential orders (up to a constant)", op)
     assert all(1.8 <= o <= 2.3 for o in oc), oc
-    # the potentials converge too, at a lower observed order (about 1.3-1.5 here)
-    assert all(o >= 1.2 for o in op), op
+    assert all(1.8 <= o <= 2.3 for o in op), op
 
 
 def test_first_order_in_time():
