@@ -237,3 +237,46 @@ def test_pin_point_far_corner():
         prob.step(1, rtol=1e-10)
         ec, ep = rel_errors(prob.state_get(), ref[n])
         assert ec <= TOL and ep <= TOL, (n, ec, ep)
+
+
+def _degenerate_cfg(kind, nx=16):
+    """2D workloads with degenerate geometry: no cell at all (pure extracellular electrodiffusion,
+    no membrane, N_i = 0) or a strip cell across the whole height (the membrane meets the outer
+    boundary)."""
+    from synth.mesh import StructuredMesh, structured_mesh
+    cfg = make_config(1).with_nx(nx)
+    coords, elems = structured_mesh(2, nx, cfg.length)
+    if kind == "no-cell":
+        tag = np.zeros(len(elems), np.int32)
+        boxes = np.zeros((0, 2, 2), np.int64)
+    else:
+        cen = coords[elems].mean(axis=1) / cfg.length
+        tag = ((cen[:, 0] > 0.25) & (cen[:, 0] < 0.75)).astype(np.int32)
+        boxes = np.array([[[nx // 4, 0], [3 * nx // 4, nx]]])
+    cfg._mesh = StructuredMesh(2, nx, coords, elems, tag, boxes, cfg.length)
+    return cfg
+
+
+@pytest.mark.parametrize("kind", ["no-cell", "strip-cell"])
+def test_degenerate_geometries(kind):
+    """Steps from a smooth non-uniform state ([k]_r (1 + 0.1 cos(pi x/L) cos(pi y/L))) match the
+    oracle on a mesh without cells and on a cell that touches the outer boundary."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = _degenerate_cfg(kind)
+    pb, s0 = oproblem.from_config(cfg)
+    t = pb.topo
+    f = lambda x: np.cos(np.pi * x[:, 0] / cfg.length) * np.cos(np.pi * x[:, 1] / cfg.length)
+    s = s0.copy()
+    if t.N_i:
+        s.c_i = s0.c_i * (1 + 0.1 * f(pb.coords[t.nodes_i]))[None, :]
+    s.c_e = s0.c_e * (1 + 0.1 * f(pb.coords[t.nodes_e]))[None, :]
+    ref = [s]
+    for _ in range(4):
+        ref.append(ostep.step(pb, ref[-1])[0])
+    _, prob = problem_from_config(cfg)
+    prob.state_set(s.c_i, s.phi_i, s.c_e, s.phi_e, s.w, s.t)
+    prob.amg_setup()
+    for n in range(1, 5):
+        prob.step(1, rtol=1e-10)
+        ec, ep = rel_errors(prob.state_get(), ref[n])
+        assert ec <= TOL and ep <= TOL, (kind, n, ec, ep)
