@@ -280,3 +280,44 @@ def test_degenerate_geometries(kind):
         prob.step(1, rtol=1e-10)
         ec, ep = rel_errors(prob.state_get(), ref[n])
         assert ec <= TOL and ep <= TOL, (kind, n, ec, ep)
+
+
+def test_full_size_bench_workload():
+    """The bench workload at its full size (64^3 HH, 1,114,732 unknowns) in the bench's launch
+    configuration (FP64 hierarchy, FGMRES(30), rtol 1e-10). The oracle cannot solve it in
+    seconds, so: the assembled operator at 20,000 sampled entries, the whole right-hand side and
+    the operator's product with a random vector against the oracle's assembly; then five steps
+    whose true residuals stay at the solver tolerance and which conserve the charge of the cell
+    and of the extracellular space (Section 2.2) to that tolerance."""
+    import scipy.sparse as sp
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2)
+    pb, s0 = oproblem.from_config(cfg)
+    A, f, _ = osystem.assemble(pb, s0)
+    _, prob = problem_from_config(cfg)
+    assert prob.n_dof == 1114732
+    prob.assemble_step()
+    Acoo = A.tocoo()
+    pick = np.random.default_rng(7).choice(Acoo.nnz, 20000, replace=False)
+    As = sp.coo_matrix((Acoo.data[pick], (Acoo.row[pick], Acoo.col[pick])), shape=A.shape)
+    assert blockscaled_entry_error(pb, As, prob.operator_entries(As.row, As.col)) < 1e-12
+    assert blockwise_vector_error(pb, prob.rhs_get(), f) < 1e-12
+    x = np.random.default_rng(8).standard_normal(A.shape[0])
+    assert blockwise_vector_error(pb, prob.apply_operator(x), A @ x) < 1e-12
+
+    g = pb.geo
+    z = pb.z
+
+    def charges(st):
+        qi = sum(z[k] * (g["M_i"] @ st["c_i"][k]) for k in range(3))
+        return np.bincount(pb.topo.node_cell_i, weights=qi), sum(z[k] * (g["M_e"] @ st["c_e"][k]).sum() for k in range(3))
+
+    scale = sum((g["M_e"] @ s0.c_e[k]).sum() for k in range(3))
+    q0 = charges(prob.state_get())
+    prob.amg_setup()
+    for _ in range(5):
+        prob.assemble_step()
+        st = prob.solve(rtol=1e-10)
+        assert st["true_relres"] < 1e-9, st
+    q1 = charges(prob.state_get())
+    assert np.abs(q1[0] - q0[0]).max() < 1e-9 * scale and abs(q1[1] - q0[1]) < 1e-9 * scale
