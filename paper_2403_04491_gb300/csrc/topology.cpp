@@ -2,8 +2,11 @@
 // (Section 3.3 spatial discretisation; Remark 4.1 point pin).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <numeric>
+#include <thread>
+#include <vector>
 
 #include "common.h"
 
@@ -35,6 +38,25 @@ double simplex_det(const double* x, int dim, const int32_t* el) {
            e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
 }
 
+// Runs f(t, begin, end) on n_threads contiguous slices of [0, n).
+template <class F>
+void parallel_slices(int n_threads, int64_t n, F f) {
+    if (n_threads <= 1) {
+        f(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_threads; ++t)
+        th.emplace_back([&, t] { f(t, n * t / n_threads, n * (t + 1) / n_threads); });
+    for (auto& x : th) x.join();
+}
+
+int topology_threads(int64_t work) {
+    if (work < (int64_t)1 << 20) return 1;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(hw ? hw : 1u, 64u));
+}
+
 }  // namespace
 
 void build_topology(knp_mesh& m) {
@@ -44,7 +66,8 @@ void build_topology(knp_mesh& m) {
     // element checks
     double max_abs = 0.0;
     for (int64_t i = 0; i < nv * dim; ++i) max_abs = std::max(max_abs, std::fabs(m.coords[i]));
-    for (int64_t e = 0; e < ne; ++e) {
+    const int nthr = topology_threads(ne * nvpe);
+    auto check_element = [&](int64_t e) {
         const int32_t* el = &m.elems[e * nvpe];
         for (int j = 0; j < nvpe; ++j)
             KNP_REQUIRE(el[j] >= 0 && el[j] < nv, KNP_ERR_INVALID_ARG, "element %lld has vertex id %d out of range",
@@ -53,20 +76,67 @@ void build_topology(knp_mesh& m) {
         double det = simplex_det(m.coords.data(), dim, el);
         KNP_REQUIRE(std::fabs(det) > 1e-14 * std::pow(max_abs, dim) && std::isfinite(det), KNP_ERR_INVALID_MESH,
                     "element %lld is degenerate", (long long)e);
+    };
+    {
+        // the first failing element of each slice, found in parallel without throwing; the
+        // lowest one is then checked again serially, which raises its error
+        std::vector<int64_t> bad(nthr, ne);
+        parallel_slices(nthr, ne, [&](int t, int64_t a, int64_t b) {
+            for (int64_t e = a; e < b; ++e) {
+                const int32_t* el = &m.elems[e * nvpe];
+                bool ok = m.tag[e] >= 0;
+                for (int j = 0; j < nvpe; ++j) ok &= el[j] >= 0 && el[j] < nv;
+                if (ok) {
+                    const double det = simplex_det(m.coords.data(), dim, el);
+                    ok = std::fabs(det) > 1e-14 * std::pow(max_abs, dim) && std::isfinite(det);
+                }
+                if (!ok) {
+                    bad[t] = e;
+                    break;
+                }
+            }
+        });
+        const int64_t first = *std::min_element(bad.begin(), bad.end());
+        if (first < ne) check_element(first);
     }
-    // facets: slot s of element e is the facet opposite local vertex s
-    std::vector<FacetKey> keys((size_t)ne * nvpe);
-    for (int64_t e = 0; e < ne; ++e) {
+    // facets: slot s of element e is the facet opposite local vertex s. The keys are bucketed by
+    // their smallest vertex id (equal facets share it), each bucket is sorted and scanned on its
+    // own, and the buckets are taken in vertex order, which is the order of one global sort.
+    auto make_key = [&](int64_t e, int s) {
         const int32_t* el = &m.elems[e * nvpe];
-        for (int s = 0; s < nvpe; ++s) {
-            FacetKey k{{-1, -1, -1}, (int32_t)e, s};
-            int c = 0;
-            for (int j = 0; j < nvpe; ++j)
-                if (j != s) k.v[c++] = el[j];
-            std::sort(k.v, k.v + dim);
-            keys[e * nvpe + s] = k;
+        FacetKey k{{-1, -1, -1}, (int32_t)e, s};
+        int c = 0;
+        for (int j = 0; j < nvpe; ++j)
+            if (j != s) k.v[c++] = el[j];
+        std::sort(k.v, k.v + dim);
+        return k;
+    };
+    const int nb = nthr > 1 ? 64 * nthr : 1;
+    auto bucket_of = [&](int32_t v0) { return (int)((int64_t)v0 * nb / nv); };
+    std::vector<int64_t> cnt((size_t)nthr * nb, 0);
+    parallel_slices(nthr, ne, [&](int t, int64_t a, int64_t b) {
+        int64_t* c = &cnt[(size_t)t * nb];
+        for (int64_t e = a; e < b; ++e)
+            for (int s = 0; s < nvpe; ++s) c[bucket_of(make_key(e, s).v[0])]++;
+    });
+    std::vector<int64_t> bstart(nb + 1, 0), pos((size_t)nthr * nb);
+    for (int b = 0; b < nb; ++b) {
+        int64_t acc = bstart[b];
+        for (int t = 0; t < nthr; ++t) {
+            pos[(size_t)t * nb + b] = acc;
+            acc += cnt[(size_t)t * nb + b];
         }
+        bstart[b + 1] = acc;
     }
+    std::vector<FacetKey> keys((size_t)ne * nvpe);
+    parallel_slices(nthr, ne, [&](int t, int64_t a, int64_t b) {
+        int64_t* p = &pos[(size_t)t * nb];
+        for (int64_t e = a; e < b; ++e)
+            for (int s = 0; s < nvpe; ++s) {
+                FacetKey k = make_key(e, s);
+                keys[p[bucket_of(k.v[0])]++] = k;
+            }
+    });
     auto less = [dim](const FacetKey& a, const FacetKey& b) {
         for (int d = 0; d < dim; ++d)
             if (a.v[d] != b.v[d]) return a.v[d] < b.v[d];
@@ -77,19 +147,44 @@ void build_topology(knp_mesh& m) {
             if (a.v[d] != b.v[d]) return false;
         return true;
     };
-    std::sort(keys.begin(), keys.end(), less);
-    std::vector<FacetKey> mem;  // intracellular side of each membrane facet
-    for (size_t i = 0; i + 1 < keys.size(); ++i) {
-        if (!same(keys[i], keys[i + 1])) continue;
-        KNP_REQUIRE(i + 2 >= keys.size() || !same(keys[i], keys[i + 2]), KNP_ERR_INVALID_MESH,
-                    "a facet is shared by more than two elements");
-        int32_t ta = m.tag[keys[i].elem], tb = m.tag[keys[i + 1].elem];
-        if (ta != tb) {
-            KNP_REQUIRE(ta == 0 || tb == 0, KNP_ERR_INVALID_MESH, "cells %d and %d share a facet", ta, tb);
-            mem.push_back(ta > 0 ? keys[i] : keys[i + 1]);
+    // per bucket: sort, then pair the equal keys; an error is recorded (not thrown) as the
+    // position of the first offending key, and raised below in bucket order
+    std::vector<std::vector<FacetKey>> mem_b(nb);
+    std::vector<int64_t> err_at(nb, -1);
+    std::vector<int> err_kind(nb, 0);
+    std::atomic<int> next{0};
+    parallel_slices(nthr, nthr, [&](int, int64_t, int64_t) {
+        for (int b = next++; b < nb; b = next++) {
+            const int64_t lo = bstart[b], hi = bstart[b + 1];
+            std::sort(keys.begin() + lo, keys.begin() + hi, less);
+            for (int64_t i = lo; i + 1 < hi; ++i) {
+                if (!same(keys[i], keys[i + 1])) continue;
+                if (i + 2 < hi && same(keys[i], keys[i + 2])) {
+                    err_at[b] = i;
+                    err_kind[b] = 1;
+                    break;
+                }
+                const int32_t ta = m.tag[keys[i].elem], tb = m.tag[keys[i + 1].elem];
+                if (ta != tb) {
+                    if (ta != 0 && tb != 0) {
+                        err_at[b] = i;
+                        err_kind[b] = 2;
+                        break;
+                    }
+                    mem_b[b].push_back(ta > 0 ? keys[i] : keys[i + 1]);
+                }
+                ++i;
+            }
         }
-        ++i;
+    });
+    for (int b = 0; b < nb; ++b) {
+        if (err_at[b] < 0) continue;
+        const FacetKey& k = keys[err_at[b]];
+        KNP_REQUIRE(err_kind[b] != 1, KNP_ERR_INVALID_MESH, "a facet is shared by more than two elements");
+        KNP_FAIL(KNP_ERR_INVALID_MESH, "cells %d and %d share a facet", m.tag[k.elem], m.tag[keys[err_at[b] + 1].elem]);
     }
+    std::vector<FacetKey> mem;  // intracellular side of each membrane facet
+    for (int b = 0; b < nb; ++b) mem.insert(mem.end(), mem_b[b].begin(), mem_b[b].end());
     // keys are sorted lexicographically, so mem is in facet order already
     const int64_t nf = (int64_t)mem.size();
     m.facets.resize(nf * dim);

@@ -148,3 +148,40 @@ def test_pin_point(lib, where):
     d = np.sum((m.coords[T.nodes_e] - pt) ** 2, axis=1)
     assert T.pin_vertex == T.nodes_e[np.flatnonzero(d == d.min())[0]]
     assert Mesh(m.coords, m.elems, m.elem_tag).info["pin_vertex"] == build_topology(m.coords, m.elems, m.elem_tag).pin_vertex
+
+
+def test_mesh_topology_matches_oracle_threaded(lib):
+    """A mesh large enough for the threaded facet matching (the 125-cell geometry at 64^3, 1.57M
+    tetrahedra): the library's facets, region nodes and pin equal the oracle's."""
+    from paper_2403_04491_gb300 import Mesh
+    cfg = make_config(3).with_nx(64)
+    m = cfg.mesh
+    M = Mesh(m.coords, m.elems, m.elem_tag)
+    T = build_topology(m.coords, m.elems, m.elem_tag)
+    ni, ne = M.nodes()
+    v, e, o, c = M.facets()
+    assert M.info["n_dof"] == T.n_dof(3)
+    assert np.array_equal(ni, T.nodes_i) and np.array_equal(ne, T.nodes_e)
+    assert np.array_equal(v, T.facets) and np.array_equal(e, T.facet_elem_i)
+    assert np.array_equal(o, T.facet_opp_i) and np.array_equal(c, T.facet_cell)
+    assert M.info["pin_vertex"] == T.pin_vertex
+
+
+def test_threaded_facet_matching_reports_invalid_meshes(lib):
+    """The threaded facet matching rejects a mesh with a facet shared by three elements (an
+    element duplicated in a large mesh) and two cells touching, as the serial one does."""
+    from paper_2403_04491_gb300 import Mesh
+    from paper_2403_04491_gb300.knp import KnpError
+    m = make_config(2).with_nx(48).mesh
+    elems = np.concatenate([m.elems, m.elems[:1]])
+    tag = np.concatenate([m.elem_tag, m.elem_tag[:1]])
+    with pytest.raises(KnpError, match="more than two"):
+        Mesh(m.coords, elems, tag)
+    tag2 = m.elem_tag.copy()
+    # a second cell right next to the first: retag the extracellular elements sharing a facet with it
+    T = build_topology(m.coords, m.elems, m.elem_tag)
+    f0 = T.facets[0]
+    share = np.flatnonzero(np.isin(m.elems, f0).sum(axis=1) == len(f0))
+    tag2[share[m.elem_tag[share] == 0]] = 2
+    with pytest.raises(KnpError, match="share a facet"):
+        Mesh(m.coords, m.elems, tag2)
