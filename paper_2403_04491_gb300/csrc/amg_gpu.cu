@@ -382,22 +382,70 @@ __global__ void k_transpose_fill(int64_t n, const int64_t* __restrict__ ptr, con
     }
 }
 
-// sort each row of a CSR4 by column (rows are short)
-__global__ void k_sort_rows(int64_t n, const int64_t* __restrict__ ptr, int32_t* __restrict__ col,
-                            double* __restrict__ val) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// sort each row of a CSR4 by column with one block per row: the (column, position) pairs of a row
+// of up to SORT_MAX entries are bitonic-sorted in shared memory and the four values gathered in
+// that order; longer rows fall back to the serial sort above. Columns within a row are distinct,
+// so the result equals that of any other sort.
+constexpr int SORT_MAX = 1024;
+constexpr int SORT_THREADS = 256;
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_rows_block(int64_t n, const int64_t* __restrict__ ptr,
+                                                                  int32_t* __restrict__ col,
+                                                                  double* __restrict__ val) {
+    __shared__ int32_t key[SORT_MAX];
+    __shared__ int32_t pos[SORT_MAX];
+    __shared__ double vs[4 * SORT_MAX];
+    const int64_t i = blockIdx.x;
     if (i >= n) return;
-    for (int64_t a = ptr[i] + 1; a < ptr[i + 1]; ++a) {
-        int32_t c = col[a];
-        double v[4] = {val[4 * a], val[4 * a + 1], val[4 * a + 2], val[4 * a + 3]};
-        int64_t b = a;
-        while (b > ptr[i] && col[b - 1] > c) {
-            col[b] = col[b - 1];
-            for (int f = 0; f < 4; ++f) val[4 * b + f] = val[4 * (b - 1) + f];
-            --b;
+    const int64_t a0 = ptr[i];
+    const int len = (int)(ptr[i + 1] - a0);
+    if (len <= 1) return;
+    if (len > SORT_MAX) {
+        if (threadIdx.x == 0) {
+            for (int64_t a = a0 + 1; a < a0 + len; ++a) {
+                int32_t c = col[a];
+                double v[4] = {val[4 * a], val[4 * a + 1], val[4 * a + 2], val[4 * a + 3]};
+                int64_t b = a;
+                while (b > a0 && col[b - 1] > c) {
+                    col[b] = col[b - 1];
+                    for (int f = 0; f < 4; ++f) val[4 * b + f] = val[4 * (b - 1) + f];
+                    --b;
+                }
+                col[b] = c;
+                for (int f = 0; f < 4; ++f) val[4 * b + f] = v[f];
+            }
         }
-        col[b] = c;
-        for (int f = 0; f < 4; ++f) val[4 * b + f] = v[f];
+        return;
+    }
+    int m = 1;
+    while (m < len) m <<= 1;
+    for (int k = threadIdx.x; k < m; k += SORT_THREADS) {
+        key[k] = k < len ? col[a0 + k] : INT32_MAX;
+        pos[k] = k;
+    }
+    for (int k = threadIdx.x; k < 4 * len; k += SORT_THREADS) vs[k] = val[4 * a0 + k];
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = threadIdx.x; k < m; k += SORT_THREADS) {
+                const int l = k ^ stride;
+                if (l > k) {
+                    const bool up = (k & size) == 0;
+                    if ((key[k] > key[l]) == up) {
+                        const int32_t tk = key[k];
+                        key[k] = key[l];
+                        key[l] = tk;
+                        const int32_t tp = pos[k];
+                        pos[k] = pos[l];
+                        pos[l] = tp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < len; k += SORT_THREADS) {
+        col[a0 + k] = key[k];
+        for (int f = 0; f < 4; ++f) val[4 * (a0 + k) + f] = vs[4 * pos[k] + f];
     }
 }
 
@@ -760,7 +808,7 @@ bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, in
             R.val.alloc(4 * R.nnz);
             k_transpose_fill<<<nb(n, 256), 256, 0, st>>>(n, P.ptr.p, P.col.p, P.val.p, R.ptr.p, fill.p, R.col.p,
                                                          R.val.p);
-            k_sort_rows<<<nb(na, 128), 128, 0, st>>>(na, R.ptr.p, R.col.p, R.val.p);
+            k_sort_rows_block<<<(unsigned)na, SORT_THREADS, 0, st>>>(na, R.ptr.p, R.col.p, R.val.p);
         }
         download(P, L.P, st);
         download(R, L.R, st);
