@@ -84,7 +84,8 @@ typedef struct {
 /* Builds the topology: membrane facets are the facets shared by an element of
  * tag 0 and one of tag >= 1; every membrane vertex gets one node in each
  * region (Section 3.3; the count of Section 5.1). The pin is the extracellular
- * vertex nearest to the origin, ties broken by lowest id (Remark 4.1).
+ * vertex nearest to desc->pin_point (the origin when NULL), ties broken by lowest
+ * id (Remark 4.1).
  * Errors: KNP_ERR_INVALID_ARG (NULL, dim not 2/3, ids out of range),
  * KNP_ERR_INVALID_MESH (zero-volume element, two cells sharing a facet or a
  * vertex, regions touching outside membrane facets, a cell with no facet). */
