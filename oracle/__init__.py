@@ -12,6 +12,7 @@ notation, with no blocking, fusion or reordering beyond the definitions:
 
 * ``topology``  - membrane facets, duplicated membrane nodes, DOF numbering (Section 3.3, Model A count of Section 5.1)
 * ``fem``       - P1 mass/stiffness/weighted-stiffness and membrane matrices (Section 4.1)
+* ``p2``        - P2 Lagrange elements: nodes, local matrices by barycentric moments, discretisation (Section 3.3 with p = 2)
 * ``membrane``  - reversal potentials, alpha, Hodgkin-Huxley gates by Rush-Larsen, channel currents (Section 2.4, 3.2)
 * ``system``    - the block operator A_{n-1}, right-hand side f_n, point pin and P_0 (Section 4.1, Remark 4.1, Eq. 4.4)
 * ``solve``     - direct sparse solve and plain restarted GMRES (Section 6.2)

@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import membrane, system
+from . import membrane, p2, system
 from .topology import build_topology
 
 
@@ -20,11 +20,19 @@ def facet_inputs(cfg, topo, coords):
     return model, gleak, mask
 
 
-def from_config(cfg, dt=None, pin_point=None):
+def from_config(cfg, dt=None, pin_point=None, degree=1):
+    """Oracle Problem and initial State; ``degree`` 1 (P1) or 2 (P2 Lagrange elements, Section 3.3)."""
     m = cfg.mesh
     p = cfg.params
-    topo = build_topology(m.coords, m.elems, m.elem_tag, pin_point=pin_point)
-    model, gleak, mask = facet_inputs(cfg, topo, m.coords)
+    if degree == 1:
+        topo = build_topology(m.coords, m.elems, m.elem_tag, pin_point=pin_point)
+        vtopo, node_coords = topo, m.coords
+    elif degree == 2:
+        topo = p2.build_topology(m.coords, m.elems, m.elem_tag, pin_point=pin_point)
+        vtopo, node_coords = topo.base, topo.node_coords
+    else:
+        raise ValueError("degree must be 1 or 2")
+    model, gleak, mask = facet_inputs(cfg, vtopo, m.coords)
     pb = system.Problem(topo=topo, coords=m.coords, elems=m.elems, R=p["R"], T=p["T"], F=p["F"],
                         Cm=p["Cm"], z=np.asarray(p["z"], float), D_i=np.asarray(p["D"], float),
                         D_e=np.asarray(p["D"], float), dt=cfg.dt if dt is None else dt,
@@ -36,10 +44,14 @@ def from_config(cfg, dt=None, pin_point=None):
                         cKe0=p["c_e0"][1])
     # E_K^0 of the Kir factor: the K reversal potential of the initial concentrations
     pb.E_K0 = float(membrane.reversal_potential(p["R"], p["T"], p["F"], p["z"][1], p["c_i0"][1], p["c_e0"][1]))
-    src = cfg.vertex_source_e()
+    src = cfg.source_e_at(node_coords[topo.nodes_e])
     if src is not None:
-        pb.source_e = np.ascontiguousarray(src[topo.nodes_e].T)
+        pb.source_e = np.ascontiguousarray(src.T)
         pb.source_t0, pb.source_t1 = cfg.source_t0, cfg.source_t1
-    system.discretize(pb)
+    if degree == 1:
+        system.discretize(pb)
+    else:
+        pb.fe = p2
+        p2.discretize(pb)
     s0 = system.initial_state(pb, p["c_i0"], p["c_e0"], p["phi_M0"], (p["n0"], p["m0"], p["h0"]))
     return pb, s0

@@ -74,6 +74,8 @@ class Problem:
     source_t0: float = 0.0
     source_t1: float = 0.0
     geo: dict = field(default_factory=dict)
+    # the finite-element space's matrix routines: fem (P1) or p2 (P2)
+    fe: object = fem
 
     @property
     def psi(self):
@@ -237,14 +239,14 @@ def assemble(pb: Problem, s: State, source=None):
         M, A = g["M_" + r], g["A_" + r]
         tau = dt * D_r
         taut = tau * z / psi
-        Ak = [fem.weighted_stiffness(g["cache_" + r], c_r[k], g["en_" + r], Nr) for k in range(K)]
+        Ak = [pb.fe.weighted_stiffness(g["cache_" + r], c_r[k], g["en_" + r], Nr) for k in range(K)]
         phi_blk = (pb.Cm / pb.F) * g["MG_" + r]
         phi_q = -(pb.Cm / pb.F) * g["MG_" + r + q]
         f_phi = np.zeros(Nr)
         I_tot = I.sum(axis=0)
         for k in range(K):
-            CM_r = fem.membrane_mass(area, fr, fr, Nr, Nr, coef=C_r[k][fv])
-            CM_rq = fem.membrane_mass(area, fr, fq, Nr, Nq, coef=C_r[k][fv])
+            CM_r = pb.fe.membrane_mass(area, fr, fr, Nr, Nr, coef=C_r[k][fv])
+            CM_rq = pb.fe.membrane_mass(area, fr, fq, Nr, Nq, coef=C_r[k][fv])
             blocks[o + k][o + k] = M + tau[k] * A
             blocks[o + k][o + K] = CM_r + taut[k] * Ak[k]
             blocks[o + k][oq + K] = -CM_rq
@@ -252,8 +254,8 @@ def assemble(pb: Problem, s: State, source=None):
             phi_blk = phi_blk + z[k] * taut[k] * Ak[k]
             # f_r^k = M c^{k,n-1} + dt M f^{k,n} - int_Gamma g_r^k v,
             # g_r^k = +-_r (dt I_ch^k - alpha_r^k C_m phi_M^{n-1}) / (F z_k)
-            ICH = fem.membrane_load(area, fr, I[k], Nr)
-            aphi = fem.membrane_mass(area, fr, fv, Nr, g["n_mv"], coef=a_r[k][fv]) @ mf["phi_M"]
+            ICH = pb.fe.membrane_load(area, fr, I[k], Nr)
+            aphi = pb.fe.membrane_mass(area, fr, fv, Nr, g["n_mv"], coef=a_r[k][fv]) @ mf["phi_M"]
             fk = M @ c_r[k] - sgn * (dt * ICH - pb.Cm * aphi) / (pb.F * z[k])
             if source is not None:
                 fk = fk + dt * (M @ source[r][k])
@@ -261,8 +263,8 @@ def assemble(pb: Problem, s: State, source=None):
         blocks[o + K][o + K] = phi_blk
         blocks[o + K][oq + K] = phi_q
         # f_r^phi = - int_Gamma h_r w,  h_r = +-_r (dt I_ch - C_m phi_M^{n-1}) / F
-        ICH = fem.membrane_load(area, fr, I_tot, Nr)
-        phiM_load = fem.membrane_load(area, fr, mf["phi_M"][fv], Nr)
+        ICH = pb.fe.membrane_load(area, fr, I_tot, Nr)
+        phiM_load = pb.fe.membrane_load(area, fr, mf["phi_M"][fv], Nr)
         rhs.append(-sgn * (dt * ICH - pb.Cm * phiM_load) / pb.F)
     # rhs order: i ions, i phi, e ions, e phi
     f = np.concatenate(rhs)
@@ -303,7 +305,7 @@ def preconditioner_P0(pb: Problem, s0: State) -> sp.csr_matrix:
             diag.append(M + tau[k] * A)
         blk = (pb.Cm / pb.F) * g["MG_" + r]
         for k in range(K):
-            blk = blk + z[k] * taut[k] * fem.weighted_stiffness(g["cache_" + r], c_r[k], g["en_" + r], Nr)
+            blk = blk + z[k] * taut[k] * pb.fe.weighted_stiffness(g["cache_" + r], c_r[k], g["en_" + r], Nr)
         diag.append(blk)
     P = sp.block_diag(diag, format="csr")
     P, _ = apply_pin(pb, P, np.zeros(P.shape[0]))

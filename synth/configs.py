@@ -85,10 +85,13 @@ class Config:
     def vertex_source_e(self) -> Optional[np.ndarray]:
         """(n_vertices, n_ions) bulk source values for the extracellular copy of each vertex:
         source_e where the vertex's x < source_xmax, else 0; None without a source."""
+        return self.source_e_at(self.mesh.coords)
+
+    def source_e_at(self, points: np.ndarray) -> Optional[np.ndarray]:
+        """(n_points, n_ions) extracellular bulk source values at arbitrary points (P2 nodes)."""
         if self.source_e is None:
             return None
-        m = self.mesh
-        on = (m.coords[:, 0] < self.source_xmax).astype(float)
+        on = (np.asarray(points)[:, 0] < self.source_xmax).astype(float)
         return on[:, None] * np.asarray(self.source_e, float)[None, :]
 
     def with_nx(self, nx: int) -> "Config":
