@@ -101,6 +101,34 @@ knp_status knp_mesh_facets(const knp_mesh* mesh, int32_t* vertices, int32_t* ele
                            int32_t* opp_i, int32_t* cell);
 void knp_mesh_destroy(knp_mesh* mesh);
 
+/* P2 nodes (Section 3.3 with polynomial degree p = 2; Section 6.3 runs p in {1, 2}). Global
+ * node ids are the vertex ids 0..n_vertices-1, then n_vertices + e for the edges e in
+ * lexicographic order of their sorted vertex pair (an edge node sits at the edge midpoint). A
+ * node belongs to a region when it is a node of one of the region's elements, so the vertices
+ * and edges of membrane facets get one node in each region; region node order is increasing
+ * global id. Built on the first call for a mesh (thread-safe), host only.
+ * Errors: KNP_ERR_INVALID_ARG (NULL, more than 2^31 - 1 nodes), KNP_ERR_INVALID_MESH (the two
+ * regions share an edge that lies in no membrane facet). */
+typedef struct {
+    int64_t n_edges;
+    int64_t n_nodes;             /* n_vertices + n_edges */
+    int64_t N_i, N_e;            /* P2 region node counts (membrane nodes counted in both) */
+    int64_t n_membrane_nodes;
+    int64_t pin_node;            /* global id of the extracellular node nearest to the pin point,
+                                    ties by lowest id (Remark 4.1) */
+    int64_t n_dof;               /* (N_i + N_e)(n_ions + 1) for n_ions = 3 */
+} knp_p2_info;
+
+knp_status knp_mesh_p2_get_info(const knp_mesh* mesh, knp_p2_info* info);
+/* P2 tables (host, caller-allocated, any may be NULL):
+ * edges[n_edges*2] sorted vertex pairs; elem_nodes[n_elems*(d+1)(d+2)/2] the element's vertices
+ * in its own order, then its edges (a, b), a < b, in lexicographic order of the local pair;
+ * facet_nodes[n_facets*d(d+1)/2] the facet's sorted vertices (knp_mesh_facets order), then its
+ * edges likewise; nodes_i[N_i], nodes_e[N_e] region node -> global id; membrane_nodes[
+ * n_membrane_nodes] increasing; node_cell_i[N_i] the cell tag of each intracellular node. */
+knp_status knp_mesh_p2_tables(const knp_mesh* mesh, int32_t* edges, int32_t* elem_nodes, int32_t* facet_nodes,
+                              int32_t* nodes_i, int32_t* nodes_e, int32_t* membrane_nodes, int32_t* node_cell_i);
+
 /* ------------------------------------------------------------------------- */
 /* Problem (Sections 2, 3.2, Table 2)                                        */
 /* ------------------------------------------------------------------------- */

@@ -3,6 +3,8 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -50,6 +52,21 @@ knp_status guarded(F&& f) {
 
 }  // namespace knp
 
+// P2 nodes of a mesh (Section 3.3 with p = 2): the vertices, then the edges in lexicographic
+// order of their sorted vertex pair; a node belongs to a region when it is a node of one of the
+// region's elements, so the vertices and edges of membrane facets are repeated.
+struct knp_p2_nodes {
+    int64_t n_edges = 0;
+    std::vector<int32_t> edges;              // [n_edges*2] sorted vertex pairs, lexicographic
+    std::vector<int32_t> elem_nodes;         // [ne*npe]: the element's vertices, then its edges (a<b)
+    std::vector<int32_t> facet_nodes;        // [nf*nfn]: the facet's sorted vertices, then its edges
+    std::vector<int32_t> nodes_i, nodes_e;   // region node -> global node id (increasing)
+    std::vector<int32_t> loc_i, loc_e;       // global node id -> region node, -1 if absent
+    std::vector<int32_t> mnodes;             // membrane nodes, increasing
+    std::vector<int32_t> node_cell_i;        // cell tag of each intracellular node
+    int64_t pin_node = -1;
+};
+
 // Topology of a conforming mesh with duplicated membrane nodes (Section 3.3).
 struct knp_mesh {
     int32_t dim = 0;
@@ -68,4 +85,12 @@ struct knp_mesh {
     double pin_point[3] = {0.0, 0.0, 0.0};   // the pin goes on the e-vertex nearest to this point
     int32_t n_cells = 0;
     int64_t nf() const { return (int64_t)facet_cell.size(); }
+    // P2 nodes, built on first use (knp_mesh_p2_*)
+    mutable std::once_flag p2_once;
+    mutable std::unique_ptr<knp_p2_nodes> p2;
 };
+
+namespace knp {
+// The P2 nodes of m, built on first call (thread-safe); throws Error on an invalid mesh.
+const knp_p2_nodes& p2_nodes(const knp_mesh& m);
+}  // namespace knp

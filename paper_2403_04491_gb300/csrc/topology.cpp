@@ -258,6 +258,135 @@ void build_topology(knp_mesh& m) {
     }
 }
 
+namespace {
+
+// Local edges (a, b), a < b, of an m-simplex in lexicographic order.
+int local_pairs(int m, int out[6][2]) {
+    int k = 0;
+    for (int a = 0; a <= m; ++a)
+        for (int b = a + 1; b <= m; ++b) {
+            out[k][0] = a;
+            out[k][1] = b;
+            ++k;
+        }
+    return k;
+}
+
+void build_p2(const knp_mesh& m, knp_p2_nodes& t) {
+    const int dim = m.dim, nvpe = dim + 1;
+    const int64_t nv = m.nv, ne = m.ne, nf = m.nf();
+    int pe[6][2], pf[6][2];
+    const int npe_edges = local_pairs(dim, pe);
+    const int nf_edges = local_pairs(dim - 1, pf);
+    auto key = [nv](int32_t a, int32_t b) {
+        return a < b ? (int64_t)a * nv + b : (int64_t)b * nv + a;
+    };
+    // edges: the sorted distinct vertex pairs of all element edges
+    std::vector<int64_t> keys((size_t)ne * npe_edges);
+    parallel_slices(topology_threads(ne * npe_edges), ne, [&](int, int64_t b, int64_t e) {
+        for (int64_t el = b; el < e; ++el) {
+            const int32_t* v = &m.elems[el * nvpe];
+            for (int k = 0; k < npe_edges; ++k) keys[el * npe_edges + k] = key(v[pe[k][0]], v[pe[k][1]]);
+        }
+    });
+    std::vector<int64_t> ek(keys);
+    std::sort(ek.begin(), ek.end());
+    ek.erase(std::unique(ek.begin(), ek.end()), ek.end());
+    t.n_edges = (int64_t)ek.size();
+    const int64_t nn = nv + t.n_edges;
+    KNP_REQUIRE(nn < INT32_MAX, KNP_ERR_INVALID_ARG, "too many P2 nodes for 32-bit ids (%lld)", (long long)nn);
+    t.edges.resize(2 * t.n_edges);
+    for (int64_t i = 0; i < t.n_edges; ++i) {
+        t.edges[2 * i] = (int32_t)(ek[i] / nv);
+        t.edges[2 * i + 1] = (int32_t)(ek[i] % nv);
+    }
+    // node id of the edge with key k, -1 if no element has it (never throws: runs on worker threads)
+    auto edge_id = [&](int64_t k) -> int32_t {
+        auto it = std::lower_bound(ek.begin(), ek.end(), k);
+        return (it != ek.end() && *it == k) ? (int32_t)(nv + (it - ek.begin())) : -1;
+    };
+    const int npe = nvpe + npe_edges;
+    t.elem_nodes.resize((size_t)ne * npe);
+    parallel_slices(topology_threads(ne * npe_edges), ne, [&](int, int64_t b, int64_t e) {
+        for (int64_t el = b; el < e; ++el) {
+            for (int j = 0; j < nvpe; ++j) t.elem_nodes[el * npe + j] = m.elems[el * nvpe + j];
+            for (int k = 0; k < npe_edges; ++k) t.elem_nodes[el * npe + nvpe + k] = edge_id(keys[el * npe_edges + k]);
+        }
+    });
+    keys.clear();
+    keys.shrink_to_fit();
+    const int nfn = dim + nf_edges;
+    t.facet_nodes.resize((size_t)nf * nfn);
+    for (int64_t f = 0; f < nf; ++f) {
+        const int32_t* v = &m.facets[f * dim];
+        for (int j = 0; j < dim; ++j) t.facet_nodes[f * nfn + j] = v[j];
+        for (int k = 0; k < nf_edges; ++k) {
+            const int32_t x = edge_id(key(v[pf[k][0]], v[pf[k][1]]));
+            KNP_REQUIRE(x >= 0, KNP_ERR_INVALID_MESH, "an edge of membrane facet %lld is not an element edge", (long long)f);
+            t.facet_nodes[f * nfn + dim + k] = x;
+        }
+    }
+    // region membership, membrane nodes and the cell of each intracellular node
+    std::vector<char> in_i(nn, 0), in_e(nn, 0), on_g(nn, 0);
+    std::vector<int32_t> cell(nn, 0);
+    for (int32_t el : m.elems_i)
+        for (int j = 0; j < npe; ++j) {
+            const int32_t x = t.elem_nodes[(int64_t)el * npe + j];
+            in_i[x] = 1;
+            cell[x] = m.tag[el];
+        }
+    for (int32_t el : m.elems_e)
+        for (int j = 0; j < npe; ++j) in_e[t.elem_nodes[(int64_t)el * npe + j]] = 1;
+    for (int32_t x : t.facet_nodes) on_g[x] = 1;
+    t.loc_i.assign(nn, -1);
+    t.loc_e.assign(nn, -1);
+    for (int64_t x = 0; x < nn; ++x) {
+        KNP_REQUIRE((in_i[x] && in_e[x]) == (bool)on_g[x], KNP_ERR_INVALID_MESH,
+                    "regions share an edge outside the membrane facets (P2 node %lld)", (long long)x);
+        if (in_i[x]) {
+            t.loc_i[x] = (int32_t)t.nodes_i.size();
+            t.nodes_i.push_back((int32_t)x);
+            t.node_cell_i.push_back(cell[x]);
+        }
+        if (in_e[x]) {
+            t.loc_e[x] = (int32_t)t.nodes_e.size();
+            t.nodes_e.push_back((int32_t)x);
+        }
+        if (on_g[x]) t.mnodes.push_back((int32_t)x);
+    }
+    // pin: extracellular node (vertex or edge midpoint) nearest to the pin point, ties by lowest id
+    double best = INFINITY;
+    for (int32_t x : t.nodes_e) {
+        double d2 = 0;
+        for (int d = 0; d < dim; ++d) {
+            double c;
+            if (x < nv) {
+                c = m.coords[(int64_t)x * dim + d];
+            } else {
+                const int64_t i = x - nv;
+                c = 0.5 * (m.coords[(int64_t)t.edges[2 * i] * dim + d] + m.coords[(int64_t)t.edges[2 * i + 1] * dim + d]);
+            }
+            const double y = c - m.pin_point[d];
+            d2 += y * y;
+        }
+        if (d2 < best) {
+            best = d2;
+            t.pin_node = x;
+        }
+    }
+}
+
+}  // namespace
+
+const knp_p2_nodes& p2_nodes(const knp_mesh& m) {
+    std::call_once(m.p2_once, [&] {
+        auto t = std::make_unique<knp_p2_nodes>();
+        build_p2(m, *t);
+        m.p2 = std::move(t);
+    });
+    return *m.p2;
+}
+
 }  // namespace knp
 
 using namespace knp;
@@ -328,6 +457,35 @@ knp_status knp_mesh_facets(const knp_mesh* m, int32_t* vertices, int32_t* elem_i
         if (elem_i) std::copy(m->facet_elem_i.begin(), m->facet_elem_i.end(), elem_i);
         if (opp_i) std::copy(m->facet_opp_i.begin(), m->facet_opp_i.end(), opp_i);
         if (cell) std::copy(m->facet_cell.begin(), m->facet_cell.end(), cell);
+    });
+}
+
+knp_status knp_mesh_p2_get_info(const knp_mesh* m, knp_p2_info* info) {
+    return guarded([&] {
+        KNP_REQUIRE(m && info, KNP_ERR_INVALID_ARG, "NULL argument");
+        const knp_p2_nodes& t = p2_nodes(*m);
+        info->n_edges = t.n_edges;
+        info->n_nodes = m->nv + t.n_edges;
+        info->N_i = (int64_t)t.nodes_i.size();
+        info->N_e = (int64_t)t.nodes_e.size();
+        info->n_membrane_nodes = (int64_t)t.mnodes.size();
+        info->pin_node = t.pin_node;
+        info->n_dof = (info->N_i + info->N_e) * 4;
+    });
+}
+
+knp_status knp_mesh_p2_tables(const knp_mesh* m, int32_t* edges, int32_t* elem_nodes, int32_t* facet_nodes,
+                              int32_t* nodes_i, int32_t* nodes_e, int32_t* membrane_nodes, int32_t* node_cell_i) {
+    return guarded([&] {
+        KNP_REQUIRE(m, KNP_ERR_INVALID_ARG, "NULL mesh");
+        const knp_p2_nodes& t = p2_nodes(*m);
+        if (edges) std::copy(t.edges.begin(), t.edges.end(), edges);
+        if (elem_nodes) std::copy(t.elem_nodes.begin(), t.elem_nodes.end(), elem_nodes);
+        if (facet_nodes) std::copy(t.facet_nodes.begin(), t.facet_nodes.end(), facet_nodes);
+        if (nodes_i) std::copy(t.nodes_i.begin(), t.nodes_i.end(), nodes_i);
+        if (nodes_e) std::copy(t.nodes_e.begin(), t.nodes_e.end(), nodes_e);
+        if (membrane_nodes) std::copy(t.mnodes.begin(), t.mnodes.end(), membrane_nodes);
+        if (node_cell_i) std::copy(t.node_cell_i.begin(), t.node_cell_i.end(), node_cell_i);
     });
 }
 

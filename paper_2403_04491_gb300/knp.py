@@ -36,6 +36,11 @@ class MeshDesc(C.Structure):
                 ("pin_point", C.POINTER(C.c_double))]
 
 
+class P2Info(C.Structure):
+    _fields_ = [("n_edges", C.c_int64), ("n_nodes", C.c_int64), ("N_i", C.c_int64), ("N_e", C.c_int64),
+                ("n_membrane_nodes", C.c_int64), ("pin_node", C.c_int64), ("n_dof", C.c_int64)]
+
+
 class MeshInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("n_elems", C.c_int64), ("N_i", C.c_int64),
                 ("N_e", C.c_int64), ("n_facets", C.c_int64), ("n_membrane_vertices", C.c_int64),
@@ -95,6 +100,8 @@ SIGNATURES = {
     "knp_mesh_nodes": [C.c_void_p, _IP, _IP],
     "knp_mesh_facets": [C.c_void_p, _IP, _IP, _IP, _IP],
     "knp_mesh_destroy": [C.c_void_p],
+    "knp_mesh_p2_get_info": [C.c_void_p, C.POINTER(P2Info)],
+    "knp_mesh_p2_tables": [C.c_void_p, _IP, _IP, _IP, _IP, _IP, _IP, _IP],
     "knp_problem_create": [C.c_void_p, C.POINTER(ProblemDesc), C.c_void_p, C.POINTER(C.c_void_p)],
     "knp_problem_destroy": [C.c_void_p],
     "knp_sync": [C.c_void_p],
@@ -195,6 +202,24 @@ class Mesh:
         c = np.empty(nf, np.int32)
         _check(_lib.knp_mesh_facets(self.handle, _iptr(v), _iptr(e), _iptr(o), _iptr(c)))
         return v, e, o, c
+
+    def p2(self):
+        """P2 nodes (knp_mesh_p2_get_info / knp_mesh_p2_tables): a dict of the info fields and tables."""
+        info = P2Info()
+        _check(_lib.knp_mesh_p2_get_info(self.handle, C.byref(info)))
+        out = {f: getattr(info, f) for f, _ in P2Info._fields_}
+        d, ne, nf = self.info["dim"], self.info["n_elems"], self.info["n_facets"]
+        t = dict(edges=np.empty((out["n_edges"], 2), np.int32),
+                 elem_nodes=np.empty((ne, (d + 1) * (d + 2) // 2), np.int32),
+                 facet_nodes=np.empty((nf, d * (d + 1) // 2), np.int32),
+                 nodes_i=np.empty(out["N_i"], np.int32), nodes_e=np.empty(out["N_e"], np.int32),
+                 membrane_nodes=np.empty(out["n_membrane_nodes"], np.int32),
+                 node_cell_i=np.empty(out["N_i"], np.int32))
+        _check(_lib.knp_mesh_p2_tables(self.handle, *(_iptr(t[k]) for k in
+                                                      ("edges", "elem_nodes", "facet_nodes", "nodes_i", "nodes_e",
+                                                       "membrane_nodes", "node_cell_i"))))
+        out.update(t)
+        return out
 
     def close(self):
         if getattr(self, "handle", None):

@@ -185,3 +185,28 @@ def test_threaded_facet_matching_reports_invalid_meshes(lib):
     tag2[share[m.elem_tag[share] == 0]] = 2
     with pytest.raises(KnpError, match="share a facet"):
         Mesh(m.coords, m.elems, tag2)
+
+
+@pytest.mark.parametrize("cfg,pin", [(make_config(1), None), (make_config(4).with_nx(64), None),
+                                     (model_a(3, 6, 1e-4), None), (make_config(3).with_nx(32), None),
+                                     (make_config(8), None), (model_a(2, 8, 1e-4), (0.55e-6, 0.02e-6))],
+                         ids=["2d-1cell", "2d-16cells", "3d-1cell", "3d-125cells", "3d-iref", "2d-pin-midpoint"])
+def test_p2_nodes_match_oracle(lib, cfg, pin):
+    """knp_mesh_p2_*: every P2 table equals the oracle's (oracle/p2.py) exactly."""
+    from oracle import p2
+    from paper_2403_04491_gb300 import Mesh
+    m = cfg.mesh
+    M = Mesh(m.coords, m.elems, m.elem_tag, pin_point=pin)
+    T = p2.build_topology(m.coords, m.elems, m.elem_tag, pin_point=pin)
+    P = M.p2()
+    assert P["n_edges"] == len(T.edges) and P["n_nodes"] == len(T.node_coords)
+    assert P["n_dof"] == T.n_dof(3)
+    for k, ref in (("edges", T.edges), ("elem_nodes", T.elem_nodes), ("facet_nodes", T.facet_nodes),
+                   ("nodes_i", T.nodes_i), ("nodes_e", T.nodes_e), ("membrane_nodes", T.membrane_nodes),
+                   ("node_cell_i", T.node_cell_i)):
+        assert np.array_equal(P[k], ref), k
+    assert P["pin_node"] == T.pin_node
+    if pin is not None:
+        assert T.pin_node >= m.coords.shape[0]      # this pin point sits nearest to an edge midpoint
+    # a second query returns the same tables (built once)
+    assert np.array_equal(M.p2()["elem_nodes"], P["elem_nodes"])
