@@ -128,6 +128,17 @@ knp_status knp_mesh_p2_get_info(const knp_mesh* mesh, knp_p2_info* info);
  * n_membrane_nodes] increasing; node_cell_i[N_i] the cell tag of each intracellular node. */
 knp_status knp_mesh_p2_tables(const knp_mesh* mesh, int32_t* edges, int32_t* elem_nodes, int32_t* facet_nodes,
                               int32_t* nodes_i, int32_t* nodes_e, int32_t* membrane_nodes, int32_t* node_cell_i);
+/* The P2 matrices M_r, A_r and A_r^{c} = [int c grad phi_j . grad phi_l] of one region (Section
+ * 4.1 with p = 2) as the element contributions, unsummed: for each element of the region (region
+ * 0 = intracellular, elements with tag >= 1 in increasing id; 1 = extracellular, tag 0) and each
+ * (j, l) of its (d+1)(d+2)/2 local nodes, rows/cols = region node indices and M/A/Ac the
+ * element's entries. c: host [N_r] nodal values of the P2 coefficient (needed for Ac only). The
+ * library's P2 problems use the same values and, per step, the same element arithmetic for
+ * A_r^{k} (Ac's diagonal is minus the off-diagonal row sum, exact since the basis sums to one).
+ * *count = n_region_elems * ((d+1)(d+2)/2)^2; any output may be NULL (all NULL: *count only).
+ * Host only. Errors: KNP_ERR_INVALID_ARG (NULL mesh or count, region not 0/1, Ac without c). */
+knp_status knp_mesh_p2_region_matrices(const knp_mesh* mesh, int32_t region, const double* c, int64_t* count,
+                                       int32_t* rows, int32_t* cols, double* M, double* A, double* Ac);
 
 /* ------------------------------------------------------------------------- */
 /* Problem (Sections 2, 3.2, Table 2)                                        */
@@ -171,6 +182,12 @@ typedef struct {
     const double* source_i;
     const double* source_e;
     double source_t0, source_t1;
+    /* polynomial degree p of the Lagrange spaces (Section 3.3): 0 or 1 = P1, 2 = P2. With P2 the
+       unknowns live on the P2 nodes of knp_mesh_p2_*: region node order, the membrane nodes
+       (gates, membrane coefficients) and the pin are those of knp_mesh_p2_tables, and source_i /
+       source_e are indexed by global P2 node id ([n_nodes * n_ions], knp_p2_info.n_nodes). The
+       adjoint step covers P1 only. */
+    int32_t degree;
 } knp_problem_desc;
 
 /* Creates device state for one simulation on `stream`; u_0 as in Section 2.3

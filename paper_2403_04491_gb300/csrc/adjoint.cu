@@ -311,6 +311,7 @@ void build_problem_stiffness(knp_problem* P, std::vector<double>& elA, std::vect
                              std::vector<int32_t>& nelist);
 
 void adjoint_begin(knp_problem* P) {
+    KNP_REQUIRE(P->degree == 1, KNP_ERR_INVALID_ARG, "the adjoint step covers P1 elements; this problem is P2");
     for (int32_t v : P->facet_model)
         KNP_REQUIRE(v != KNP_MODEL_KIR, KNP_ERR_INVALID_ARG,
                     "the adjoint step covers leak and HH facets; this problem has Kir-Na/K facets");

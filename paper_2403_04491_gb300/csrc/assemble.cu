@@ -7,6 +7,11 @@
 //                    and the bulk right-hand side M c^{k,n-1}
 //   membrane_pairs   C_r^k-weighted membrane mass on same-region and cross-region entries
 //   membrane_rhs     -int g_r^k v and -int h_r w at membrane nodes
+// P2 elements replace elem_means by element pair values and use the P2 facet basis in the two
+// membrane kernels (the P2 section at the end of the anonymous namespace).
+#include <mutex>
+
+#include "p2_pairs.cuh"
 #include "problem.h"
 
 namespace knp {
@@ -247,6 +252,186 @@ __global__ void k_membrane_rhs(StepParams sp, int64_t nmv, int dim, int32_t pin,
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// ---- P2 elements (Section 3.3 with p = 2) -------------------------------------------------------
+// The membrane update, the row pass and the edge sums are the P1 kernels; the element pair values
+// of A_r^{k} and the membrane integrals with the P2 facet basis are computed here.
+
+__constant__ P2Dev c_p2[2];   // element dimension 2 and 3
+
+// V[k][e * npairs + p] = int_T [k]^{n-1} grad phi_j . grad phi_l for the off-diagonal local pair p
+// = (j, l) of element e (p2_pair_values).
+template <int D>
+__global__ void __launch_bounds__(128) k_p2_elem_pairs(int64_t ne, const int32_t* __restrict__ eln,
+                                                       const double* __restrict__ elg, const double* __restrict__ u,
+                                                       double* __restrict__ V) {
+    constexpr int NPE = (D + 1) * (D + 2) / 2;
+    constexpr int NPAIR = NPE * (NPE - 1) / 2;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    double G[16];
+    for (int i = 0; i < 16; ++i) G[i] = elg[e * 16 + i];
+    int32_t g[NPE];
+    for (int j = 0; j < NPE; ++j) g[j] = eln[e * NPE + j];
+    const int64_t nslot = ne * NPAIR;
+    for (int k = 0; k < KI; ++k) {
+        double c[NPE], out[NPAIR];
+        for (int j = 0; j < NPE; ++j) c[j] = u[4 * (int64_t)g[j] + k];
+        p2_pair_values<D>(c_p2[D - 2], G, c, out);
+        for (int p = 0; p < NPAIR; ++p) V[k * nslot + e * NPAIR + p] = out[p];
+    }
+}
+
+// C_r^k-weighted P2 membrane mass on same-region and cross-region entries (cf. k_membrane_pairs)
+template <int D>
+__global__ void k_membrane_pairs_p2(int64_t npairs, int64_t nmv, int64_t n_entries, int64_t n_cross,
+                                    const int32_t* __restrict__ mp_ptr, const int32_t* __restrict__ mpf,
+                                    const int32_t* __restrict__ tgt, const int32_t* __restrict__ fmv,
+                                    const double* __restrict__ area, const double* __restrict__ mf,
+                                    double* __restrict__ e, double* __restrict__ xe) {
+    constexpr int NFN = D * (D + 1) / 2;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= npairs) return;
+    const P2Dev& T = c_p2[D - 2];
+    double vi[KI] = {0, 0, 0}, ve[KI] = {0, 0, 0};
+    for (int q = mp_ptr[t]; q < mp_ptr[t + 1]; ++q) {
+        const int32_t pk = mpf[q];
+        const int64_t f = pk >> 6;
+        const int sa = (pk >> 3) & 7, sb = pk & 7;
+        const double A = area[f];
+        for (int c = 0; c < NFN; ++c) {
+            const int64_t mvc = fmv[f * NFN + c];
+            const double W = A * T.ftriple[c][sa][sb];
+            for (int k = 0; k < KI; ++k) {
+                vi[k] += W * mf[(1 + k) * nmv + mvc];
+                ve[k] += W * mf[(4 + k) * nmv + mvc];
+            }
+        }
+    }
+    const int32_t* tg = tgt + 4 * t;
+    for (int k = 0; k < KI; ++k) {
+        e[k * n_entries + tg[0]] += vi[k];
+        e[k * n_entries + tg[1]] += ve[k];
+        xe[k * n_cross + tg[2]] = -vi[k];
+        xe[k * n_cross + tg[3]] = -ve[k];
+    }
+}
+
+// -int_Gamma g_r^k v and -int_Gamma h_r w at the P2 membrane nodes (cf. k_membrane_rhs)
+template <int D>
+__global__ void k_membrane_rhs_p2(StepParams sp, int64_t nmv, int32_t pin, const int32_t* __restrict__ mv_g,
+                                  const int32_t* __restrict__ mvf_ptr, const int32_t* __restrict__ mvf,
+                                  const int32_t* __restrict__ fmv, const double* __restrict__ area,
+                                  const int32_t* __restrict__ fmodel, const double* __restrict__ fgleak,
+                                  const uint8_t* __restrict__ fmask, const double* __restrict__ mf,
+                                  double* __restrict__ f) {
+    constexpr int NFN = D * (D + 1) / 2;
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= nmv) return;
+    const P2Dev& T = c_p2[D - 2];
+    double intI[KI] = {0, 0, 0}, cphi_i[KI] = {0, 0, 0}, cphi_e[KI] = {0, 0, 0}, intPhi = 0;
+    for (int q = mvf_ptr[a]; q < mvf_ptr[a + 1]; ++q) {
+        const int64_t fid = mvf[q] >> 3;
+        const int s = mvf[q] & 7;
+        const double A = area[fid];
+        const bool hh = fmodel[fid] == KNP_MODEL_HH, kir = fmodel[fid] == KNP_MODEL_KIR;
+        const double gst = fmask[fid] ? sp.g_stim : 0.0;
+        double gl[KI];
+        for (int k = 0; k < KI; ++k) gl[k] = fgleak[fid * KI + k];
+        for (int c = 0; c < NFN; ++c) {
+            const int64_t mc = fmv[fid * NFN + c];
+            const double Mcs = A * T.fmass[c][s];
+            double I[KI];
+            for (int k = 0; k < KI; ++k) I[k] = gl[k] * mf[(7 + k) * nmv + mc];
+            I[sp.ion_na] += gst * mf[(7 + sp.ion_na) * nmv + mc];
+            if (hh) {
+                I[sp.ion_na] += sp.gbar_na * mf[10 * nmv + mc];
+                I[sp.ion_k] += sp.gbar_k * mf[11 * nmv + mc];
+            }
+            if (kir) {
+                const double j = mf[13 * nmv + mc];
+                I[sp.ion_k] = gl[sp.ion_k] * mf[12 * nmv + mc] - 2.0 * sp.F * sp.z[sp.ion_k] * j;
+                I[sp.ion_na] += 3.0 * sp.F * sp.z[sp.ion_na] * j;
+            }
+            for (int k = 0; k < KI; ++k) intI[k] += Mcs * I[k];
+            intPhi += Mcs * mf[mc];
+            for (int b = 0; b < NFN; ++b) {
+                const int64_t mb = fmv[fid * NFN + b];
+                const double W = A * T.ftriple[c][b][s] * mf[mb];
+                for (int k = 0; k < KI; ++k) {
+                    cphi_i[k] += W * mf[(1 + k) * nmv + mc];
+                    cphi_e[k] += W * mf[(4 + k) * nmv + mc];
+                }
+            }
+        }
+    }
+    const int64_t gi = mv_g[a], ge = mv_g[nmv + a];
+    double Itot = 0;
+    for (int k = 0; k < KI; ++k) {
+        const double jk = sp.dt * intI[k] / (sp.F * sp.z[k]);
+        f[4 * gi + k] -= jk - cphi_i[k];
+        f[4 * ge + k] += jk - cphi_e[k];
+        Itot += intI[k];
+    }
+    const double hphi = (sp.dt * Itot - sp.Cm * intPhi) / sp.F;
+    f[4 * gi + 3] -= hphi;
+    if (ge != pin) f[4 * ge + 3] += hphi;
+}
+
+template <int D>
+void launch_assembly_p2_dim(knp_problem* P, const StepParams& sp, const double* src) {
+    cudaStream_t st = P->stream;
+    const int64_t n = P->n_nodes, nmv = P->n_mv, ne = P->n_elem;
+    constexpr int NPE = (D + 1) * (D + 2) / 2;
+    const int64_t nslot = ne * (NPE * (NPE - 1) / 2);
+    count_launch(2 + (nmv ? 2 : 0) + (P->n_edges ? 1 : 0) + (P->n_pairs ? 1 : 0));
+    if (nmv) k_membrane_nodes<<<nblk(nmv, 128), 128, 0, st>>>(sp, nmv, P->mv_g.p, P->u.p, P->gates.p, P->gates_new.p,
+                                                         P->mfield.p);
+    k_p2_elem_pairs<D><<<nblk(ne, 128), 128, 0, st>>>(ne, P->el_nodes.p, P->el_g.p, P->u.p, P->cbar.p);
+    if (P->n_edges)
+        k_edge_values<<<nblk(P->n_edges), 256, 0, st>>>(P->n_edges, nslot, P->eptr.p, P->einc.p, P->ecoef.p,
+                                                        P->cbar.p, P->ak.p);
+    k_row_assemble<<<nblk(n, 128), 128, 0, st>>>(sp, n, P->N_i, P->pin, P->sell.n_entries, P->n_edges,
+                                            P->sell.slice_ptr.p, P->sell.col.p, P->sell_edge.p, P->sell_m.p,
+                                            P->ak.p, P->u.p, src, sp.dt, P->sell_e.p, P->f.p);
+    if (P->n_pairs)
+        k_membrane_pairs_p2<D><<<nblk(P->n_pairs, 128), 128, 0, st>>>(
+            P->n_pairs, nmv, P->sell.n_entries, (int64_t)P->h_xcol.size(), P->mp_ptr.p, P->mpf.p, P->mp_tgt.p,
+            P->f_mv.p, P->f_area.p, P->mfield.p, P->sell_e.p, P->xe.p);
+    if (nmv)
+        k_membrane_rhs_p2<D><<<nblk(nmv, 128), 128, 0, st>>>(sp, nmv, P->pin, P->mv_g.p, P->mvf_ptr.p, P->mvf.p,
+                                                        P->f_mv.p, P->f_area.p, P->f_model.p, P->f_gleak.p,
+                                                        P->f_mask.p, P->mfield.p, P->f.p);
+}
+
+}  // namespace
+
+void p2_upload_tables(cudaStream_t st) {
+    static P2Dev host[2];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        host[0] = p2_dev(2);
+        host[1] = p2_dev(3);
+    });
+    KNP_CUDA(cudaMemcpyToSymbolAsync(c_p2, host, sizeof(host), 0, cudaMemcpyHostToDevice, st));
+}
+
+namespace {
+
+void launch_assembly_p2(knp_problem* P) {
+    StepParams sp = P->sp;
+    sp.g_stim = stimulus_at(P->desc, P->t);
+    const double t_n = P->t + sp.dt;
+    const double* src =
+        (P->src.p && P->desc.source_t0 < t_n && t_n <= P->desc.source_t1) ? P->src.p : nullptr;
+    ProfScope ps(&P->prof, KC_ASSEMBLY, P->stream);
+    if (P->dim == 2)
+        launch_assembly_p2_dim<2>(P, sp, src);
+    else
+        launch_assembly_p2_dim<3>(P, sp, src);
+    KNP_CUDA(cudaGetLastError());
+    P->assembled = true;
+}
+
 }  // namespace
 
 double stimulus_at(const knp_problem_desc& d, double t) {
@@ -261,6 +446,10 @@ double stimulus_at(const knp_problem_desc& d, double t) {
 }
 
 void launch_assembly(knp_problem* P) {
+    if (P->degree == 2) {
+        launch_assembly_p2(P);
+        return;
+    }
     cudaStream_t st = P->stream;
     StepParams sp = P->sp;
     sp.g_stim = stimulus_at(P->desc, P->t);

@@ -72,6 +72,9 @@ knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc
         KNP_REQUIRE(mesh && desc && out, KNP_ERR_INVALID_ARG, "NULL argument");
         *out = nullptr;
         check_desc(mesh, desc);
+        KNP_REQUIRE(desc->degree >= 0 && desc->degree <= 2, KNP_ERR_INVALID_ARG, "degree must be 0, 1 or 2 (got %d)",
+                    desc->degree);
+        const int32_t degree = desc->degree == 2 ? 2 : 1;
         auto P = std::make_unique<knp_problem>();
         P->mesh = mesh;
         P->stream = (cudaStream_t)stream;
@@ -90,7 +93,8 @@ knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc
                             desc->c_e0[desc->ion_k] > 0,
                         KNP_ERR_INVALID_ARG, "Kir-Na/K facets need rho_pump >= 0, P_na, P_k > 0 and positive K "
                                              "initial concentrations");
-        const int64_t nv = mesh->nv;
+        // source arrays: per vertex (P1) or per global P2 node (P2)
+        const int64_t nv = degree == 2 ? mesh->nv + p2_nodes(*mesh).n_edges : mesh->nv;
         const double* srcs[2] = {desc->source_i, desc->source_e};
         for (int r = 0; r < 2; ++r) {
             if (!srcs[r]) continue;
@@ -136,7 +140,11 @@ knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc
         sp.EK0 = (kir) ? desc->R * desc->T / (desc->F * desc->z[desc->ion_k]) *
                              std::log(desc->c_e0[desc->ion_k] / desc->c_i0[desc->ion_k])
                        : 0.0;
-        build_problem(P.get());
+        P->degree = degree;
+        if (degree == 2)
+            build_problem_p2(P.get());
+        else
+            build_problem(P.get());
         *out = P.release();
     });
 }

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "p2_pairs.cuh"
 #include "problem.h"
 
 namespace knp {
@@ -446,6 +447,372 @@ void build_problem(knp_problem* P) {
     KNP_CUDA(cudaStreamSynchronize(st));
 }
 
+// ---- P2 elements (Section 3.3 with p = 2) ---------------------------------------------------
+
+namespace {
+
+// |T| grad lambda_a . grad lambda_b, and the P2 element mass and stiffness (Section 4.1).
+void p2_element(const double* x, int dim, const int32_t* el, const P2Ref& R, double Gm[4][4],
+                double Me[P2_NPE_MAX][P2_NPE_MAX], double Ae[P2_NPE_MAX][P2_NPE_MAX]) {
+    double vol, G[4][3];
+    simplex_geometry(x, dim, el, vol, G);
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            double s = 0.0;
+            if (a <= dim && b <= dim)
+                for (int d = 0; d < dim; ++d) s += G[a][d] * G[b][d];
+            Gm[a][b] = vol * s;
+        }
+    for (int j = 0; j < R.npe; ++j)
+        for (int l = 0; l < R.npe; ++l) {
+            double s = 0.0;
+            for (int a = 0; a <= dim; ++a)
+                for (int b = 0; b <= dim; ++b) s += R.stiff[j][l][a][b] * Gm[a][b];
+            Me[j][l] = vol * R.mass[j][l];
+            Ae[j][l] = s;
+        }
+}
+
+}  // namespace
+
+// Problem creation for P2 elements: the same operator layout as build_problem (sliced-ELL
+// region pattern with static m, a per entry; cross-region membrane CSR; node-major vectors),
+// with P2 nodes. The per-step weighted stiffness comes from element pair values (one per
+// element and off-diagonal local pair) summed over the incidences of each undirected entry.
+void build_problem_p2(knp_problem* P) {
+    const knp_mesh& m = *P->mesh;
+    const knp_p2_nodes& t2 = p2_nodes(m);
+    const int dim = m.dim, nvpe = dim + 1;
+    const P2Ref& R = p2_ref(dim);
+    const int npe = R.npe, nfn = R.nfn, npairs = R.npairs;
+    const int64_t Ni = (int64_t)t2.nodes_i.size(), Ne = (int64_t)t2.nodes_e.size();
+    const int64_t n = Ni + Ne;
+    P->dim = dim;
+    P->degree = 2;
+    P->npe = npe;
+    P->nfn = nfn;
+    P->N_i = Ni;
+    P->N_e = Ne;
+    P->n_nodes = n;
+    P->n_mv = (int64_t)t2.mnodes.size();
+    P->nf = m.nf();
+    P->n_elem = m.ne;
+    P->pin = (int32_t)(Ni + t2.loc_e[t2.pin_node]);
+    KNP_REQUIRE(m.ne * npairs < INT32_MAX, KNP_ERR_INVALID_ARG, "too many P2 element pairs for 32-bit slots");
+    KNP_REQUIRE(P->nf < (1 << 25), KNP_ERR_INVALID_ARG, "too many membrane facets for the P2 tables");
+    cudaStream_t st = P->stream;
+
+    // ---- elements with global node ids (intracellular first, then extracellular)
+    std::vector<int32_t> eln((size_t)m.ne * npe);
+    std::vector<int32_t> elem_src(m.ne);
+    {
+        int64_t k = 0;
+        for (int32_t e : m.elems_i) {
+            for (int j = 0; j < npe; ++j) eln[k * npe + j] = t2.loc_i[t2.elem_nodes[(int64_t)e * npe + j]];
+            elem_src[k++] = e;
+        }
+        for (int32_t e : m.elems_e) {
+            for (int j = 0; j < npe; ++j)
+                eln[k * npe + j] = (int32_t)(Ni + t2.loc_e[t2.elem_nodes[(int64_t)e * npe + j]]);
+            elem_src[k++] = e;
+        }
+    }
+    // ---- node -> element incidence, then sorted neighbour lists per row
+    std::vector<int64_t> ne_ptr(n + 1, 0);
+    for (int64_t e = 0; e < m.ne; ++e)
+        for (int j = 0; j < npe; ++j) ne_ptr[eln[e * npe + j] + 1]++;
+    for (int64_t i = 0; i < n; ++i) ne_ptr[i + 1] += ne_ptr[i];
+    std::vector<int32_t> ne_list(ne_ptr[n]);
+    {
+        std::vector<int64_t> fill(ne_ptr.begin(), ne_ptr.end() - 1);
+        for (int64_t e = 0; e < m.ne; ++e)
+            for (int j = 0; j < npe; ++j) ne_list[fill[eln[e * npe + j]]++] = (int32_t)e;
+    }
+    std::vector<int32_t> row_len(n);
+    std::vector<std::vector<int32_t>> rows(n);
+    for (int64_t r = 0; r < n; ++r) {
+        auto& v = rows[r];
+        for (int64_t q = ne_ptr[r]; q < ne_ptr[r + 1]; ++q)
+            for (int j = 0; j < npe; ++j) v.push_back(eln[(int64_t)ne_list[q] * npe + j]);
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        row_len[r] = (int32_t)v.size();
+    }
+    // ---- sliced ELL
+    SellPattern& S = P->sell;
+    S.n_rows = n;
+    S.n_slices = (n + SELL_C - 1) / SELL_C;
+    S.h_slice_ptr.assign(S.n_slices + 1, 0);
+    for (int64_t s = 0; s < S.n_slices; ++s) {
+        int32_t w = 0;
+        for (int64_t r = s * SELL_C; r < std::min<int64_t>(n, (s + 1) * SELL_C); ++r) w = std::max(w, row_len[r]);
+        S.h_slice_ptr[s + 1] = S.h_slice_ptr[s] + (int64_t)w * SELL_C;
+    }
+    S.n_entries = S.h_slice_ptr[S.n_slices];
+    KNP_REQUIRE(S.n_entries < INT32_MAX, KNP_ERR_INVALID_ARG, "pattern too large for 32-bit positions");
+    S.h_col.assign(S.n_entries, 0);
+    std::vector<int32_t> h_edge(S.n_entries, -2);
+    for (int64_t s = 0; s < S.n_slices; ++s) {
+        int64_t w = (S.h_slice_ptr[s + 1] - S.h_slice_ptr[s]) / SELL_C;
+        for (int64_t lane = 0; lane < SELL_C; ++lane) {
+            int64_t r = s * SELL_C + lane;
+            for (int64_t k = 0; k < w; ++k) {
+                int64_t pos = S.h_slice_ptr[s] + k * SELL_C + lane;
+                S.h_col[pos] = (r < n && k < row_len[r]) ? rows[r][k] : (int32_t)std::min<int64_t>(r, n - 1);
+            }
+        }
+    }
+    // ---- undirected entries j < l and their ids on both directed entries
+    int64_t n_edges = 0;
+    for (int64_t r = 0; r < n; ++r)
+        for (int32_t k = 0; k < row_len[r]; ++k) {
+            int32_t c = rows[r][k];
+            int64_t pos = S.h_slice_ptr[r / SELL_C] + (int64_t)k * SELL_C + r % SELL_C;
+            if (c == r)
+                h_edge[pos] = -1;
+            else if (c > r)
+                h_edge[pos] = (int32_t)n_edges++;
+        }
+    for (int64_t r = 0; r < n; ++r)
+        for (int32_t k = 0; k < row_len[r]; ++k) {
+            int32_t c = rows[r][k];
+            if (c < r) {
+                int64_t pos = S.h_slice_ptr[r / SELL_C] + (int64_t)k * SELL_C + r % SELL_C;
+                h_edge[pos] = h_edge[sell_find(S, row_len, c, (int32_t)r)];
+            }
+        }
+    P->n_edges = n_edges;
+    rows.clear();
+    rows.shrink_to_fit();
+    // ---- static M and A; |T| G per element; the (element, pair) incidences of each undirected entry
+    std::vector<double> hm(S.n_entries, 0.0), ha(S.n_entries, 0.0), hg((size_t)m.ne * 16);
+    std::vector<int32_t> e_cnt(n_edges + 1, 0);
+    for (int64_t e = 0; e < m.ne; ++e) {
+        double Gm[4][4], Me[P2_NPE_MAX][P2_NPE_MAX], Ae[P2_NPE_MAX][P2_NPE_MAX];
+        p2_element(m.coords.data(), dim, &m.elems[(int64_t)elem_src[e] * nvpe], R, Gm, Me, Ae);
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) hg[e * 16 + a * 4 + b] = Gm[a][b];
+        for (int j = 0; j < npe; ++j)
+            for (int l = 0; l < npe; ++l) {
+                int64_t pos = sell_find(S, row_len, eln[e * npe + j], eln[e * npe + l]);
+                hm[pos] += Me[j][l];
+                ha[pos] += Ae[j][l];
+            }
+        for (int p = 0; p < npairs; ++p) {
+            int64_t pos = sell_find(S, row_len, eln[e * npe + R.pj[p]], eln[e * npe + R.pl[p]]);
+            e_cnt[h_edge[pos] + 1]++;
+        }
+    }
+    for (int64_t i = 0; i < n_edges; ++i) e_cnt[i + 1] += e_cnt[i];
+    P->n_edge_inc = e_cnt[n_edges];
+    std::vector<int32_t> h_einc(e_cnt[n_edges]);
+    std::vector<double> h_ecoef(e_cnt[n_edges], 1.0);
+    {
+        std::vector<int32_t> fill(e_cnt.begin(), e_cnt.end() - 1);
+        for (int64_t e = 0; e < m.ne; ++e)
+            for (int p = 0; p < npairs; ++p) {
+                int32_t id = h_edge[sell_find(S, row_len, eln[e * npe + R.pj[p]], eln[e * npe + R.pl[p]])];
+                h_einc[fill[id]++] = (int32_t)(e * npairs + p);
+            }
+    }
+    // ---- membrane: the P2 nodes of Gamma, facet tables, node -> facet and pair -> facet incidences
+    const int64_t nmv = P->n_mv, nf = P->nf;
+    std::vector<int32_t> h_mvg(2 * nmv);
+    for (int64_t a = 0; a < nmv; ++a) {
+        int32_t x = t2.mnodes[a];
+        h_mvg[a] = t2.loc_i[x];
+        h_mvg[nmv + a] = (int32_t)(Ni + t2.loc_e[x]);
+    }
+    std::vector<int32_t> h_fmv(nf * nfn);
+    std::vector<double> h_farea(nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        for (int s = 0; s < nfn; ++s) {
+            int32_t x = t2.facet_nodes[f * nfn + s];
+            h_fmv[f * nfn + s] = (int32_t)(std::lower_bound(t2.mnodes.begin(), t2.mnodes.end(), x) - t2.mnodes.begin());
+        }
+        h_farea[f] = facet_area(m.coords.data(), dim, &m.facets[f * dim]);
+    }
+    std::vector<int32_t> h_mvf_ptr(nmv + 1, 0);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int s = 0; s < nfn; ++s) h_mvf_ptr[h_fmv[f * nfn + s] + 1]++;
+    for (int64_t a = 0; a < nmv; ++a) h_mvf_ptr[a + 1] += h_mvf_ptr[a];
+    std::vector<int32_t> h_mvf(h_mvf_ptr[nmv]);
+    {
+        std::vector<int32_t> fill(h_mvf_ptr.begin(), h_mvf_ptr.end() - 1);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int s = 0; s < nfn; ++s) h_mvf[fill[h_fmv[f * nfn + s]]++] = (int32_t)((f << 3) | s);
+    }
+    struct PairInc {
+        int64_t key;
+        int32_t packed;
+    };
+    std::vector<PairInc> pinc;
+    pinc.reserve(nf * nfn * nfn);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int sa = 0; sa < nfn; ++sa)
+            for (int sb = 0; sb < nfn; ++sb) {
+                int64_t a = h_fmv[f * nfn + sa], b = h_fmv[f * nfn + sb];
+                pinc.push_back({a * nmv + b, (int32_t)((f << 6) | (sa << 3) | sb)});
+            }
+    std::sort(pinc.begin(), pinc.end(), [](const PairInc& x, const PairInc& y) {
+        return x.key < y.key || (x.key == y.key && x.packed < y.packed);
+    });
+    std::vector<int64_t> pair_key;
+    std::vector<int32_t> h_mp_ptr(1, 0), h_mpf;
+    for (size_t i = 0; i < pinc.size(); ++i) {
+        if (i == 0 || pinc[i].key != pinc[i - 1].key) {
+            pair_key.push_back(pinc[i].key);
+            h_mp_ptr.push_back(h_mp_ptr.back());
+        }
+        h_mpf.push_back(pinc[i].packed);
+        h_mp_ptr.back()++;
+    }
+    const int64_t npairs_m = (int64_t)pair_key.size();
+    P->n_pairs = npairs_m;
+    std::vector<int32_t>& xp = P->h_xptr;
+    std::vector<int32_t>& xc = P->h_xcol;
+    xp.assign(n + 1, 0);
+    for (int64_t q = 0; q < npairs_m; ++q) {
+        int64_t a = pair_key[q] / nmv;
+        xp[h_mvg[a] + 1]++;
+        xp[h_mvg[nmv + a] + 1]++;
+    }
+    for (int64_t r = 0; r < n; ++r) xp[r + 1] += xp[r];
+    xc.assign(xp[n], 0);
+    std::vector<int32_t> h_tgt(4 * npairs_m);
+    {
+        std::vector<int32_t> fill(xp.begin(), xp.end() - 1);
+        for (int64_t q = 0; q < npairs_m; ++q) {
+            int64_t a = pair_key[q] / nmv, b = pair_key[q] % nmv;
+            int32_t gia = h_mvg[a], gea = h_mvg[nmv + a], gib = h_mvg[b], geb = h_mvg[nmv + b];
+            h_tgt[4 * q + 0] = (int32_t)sell_find(S, row_len, gia, gib);
+            h_tgt[4 * q + 1] = (int32_t)sell_find(S, row_len, gea, geb);
+            KNP_REQUIRE(h_tgt[4 * q] >= 0 && h_tgt[4 * q + 1] >= 0, KNP_ERR_INVALID_MESH,
+                        "membrane facet node pair missing from the region pattern");
+            xc[fill[gia]] = geb;
+            h_tgt[4 * q + 2] = fill[gia]++;
+            xc[fill[gea]] = gib;
+            h_tgt[4 * q + 3] = fill[gea]++;
+        }
+    }
+    std::vector<int32_t> xtp(n + 1, 0), xtr(xc.size()), xti(xc.size());
+    for (size_t q = 0; q < xc.size(); ++q) xtp[xc[q] + 1]++;
+    for (int64_t r = 0; r < n; ++r) xtp[r + 1] += xtp[r];
+    {
+        std::vector<int32_t> fill(xtp.begin(), xtp.end() - 1);
+        for (int64_t r = 0; r < n; ++r)
+            for (int32_t q = xp[r]; q < xp[r + 1]; ++q) {
+                int32_t o = fill[xc[q]]++;
+                xtr[o] = (int32_t)r;
+                xti[o] = q;
+            }
+    }
+
+    // ---- uploads
+    p2_upload_tables(st);
+    S.slice_ptr.upload(S.h_slice_ptr, st);
+    S.col.upload(S.h_col, st);
+    P->sell_edge.upload(h_edge, st);
+    P->sell_m.upload(hm, st);
+    P->sell_a.upload(ha, st);
+    P->sell_e.alloc(3 * S.n_entries);
+    P->sell_e.zero(st);
+    P->xptr.upload(xp, st);
+    P->xcol.upload(xc, st);
+    P->xtptr.upload(xtp, st);
+    P->xtrow.upload(xtr, st);
+    P->xtidx.upload(xti, st);
+    P->xe.alloc(std::max<int64_t>(1, 3 * (int64_t)xc.size()));
+    P->xe.zero(st);
+    P->el_nodes.upload(eln, st);
+    P->el_g.upload(hg, st);
+    P->cbar.alloc(3 * m.ne * npairs);
+    P->eptr.upload(e_cnt, st);
+    P->einc.upload(h_einc, st);
+    P->ecoef.upload(h_ecoef, st);
+    P->ak.alloc(std::max<int64_t>(1, 3 * n_edges));
+    P->mv_g.upload(h_mvg, st);
+    P->gates.alloc(3 * nmv);
+    P->gates_new.alloc(3 * nmv);
+    P->mfield.alloc(14 * nmv);
+    P->f_mv.upload(h_fmv, st);
+    P->f_area.upload(h_farea, st);
+    P->f_model.upload(P->facet_model, st);
+    P->f_gleak.upload(P->facet_gleak, st);
+    P->f_mask.upload(P->stim_mask, st);
+    P->mvf_ptr.upload(h_mvf_ptr, st);
+    P->mvf.upload(h_mvf, st);
+    P->mp_ptr.upload(h_mp_ptr, st);
+    P->mpf.upload(h_mpf, st);
+    P->mp_tgt.upload(h_tgt, st);
+    if (!P->source_v[0].empty() || !P->source_v[1].empty()) {
+        // bulk source at the P2 nodes (source arrays are indexed by global P2 node id)
+        std::vector<double> hs(4 * n, 0.0);
+        for (int r = 0; r < 2; ++r) {
+            if (P->source_v[r].empty()) continue;
+            const std::vector<int32_t>& nodes = r == 0 ? t2.nodes_i : t2.nodes_e;
+            const int64_t off = r == 0 ? 0 : Ni;
+            for (size_t j = 0; j < nodes.size(); ++j)
+                for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)nodes[j] * KI + k];
+        }
+        P->src.upload(hs, st);
+    }
+    P->u.alloc(4 * n);
+    P->f.alloc(4 * n);
+    P->f.zero(st);
+    P->sinv.alloc(4 * n);
+    P->svec.alloc(4 * n);
+    P->swt.alloc(4 * n);
+    const knp_problem_desc& d = P->desc;
+    count_launch(nmv ? 2 : 1);
+    k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
+                                          d.c_e0[2], d.phi_M0);
+    if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
+    KNP_CUDA(cudaGetLastError());
+    KNP_CUDA(cudaStreamSynchronize(st));
+}
+
+// Element contributions to the P2 matrices M_r, A_r and A_r^{c} of one region (host only). The
+// weighted stiffness uses the per-step kernel's pair values (p2_pair_values), with each element
+// diagonal entry minus its row's off-diagonal sum, as the row pass does for the assembled matrix.
+void p2_region_triplets(const knp_mesh& m, int region, const double* c, int32_t* rows, int32_t* cols, double* M,
+                        double* A, double* Ac) {
+    const knp_p2_nodes& t2 = p2_nodes(m);
+    const int dim = m.dim;
+    const P2Ref& R = p2_ref(dim);
+    const P2Dev& T = p2_dev(dim);
+    const int npe = R.npe;
+    const std::vector<int32_t>& els = region == 0 ? m.elems_i : m.elems_e;
+    const std::vector<int32_t>& loc = region == 0 ? t2.loc_i : t2.loc_e;
+    int64_t k = 0;
+    for (int32_t e : els) {
+        double Gm[4][4], Me[P2_NPE_MAX][P2_NPE_MAX], Ae[P2_NPE_MAX][P2_NPE_MAX];
+        p2_element(m.coords.data(), dim, &m.elems[(int64_t)e * (dim + 1)], R, Gm, Me, Ae);
+        double Ce[P2_NPE_MAX][P2_NPE_MAX] = {};
+        if (Ac) {
+            double ce[P2_NPE_MAX], pv[P2_NPAIR_MAX];
+            for (int j = 0; j < npe; ++j) ce[j] = c[loc[t2.elem_nodes[(int64_t)e * npe + j]]];
+            if (dim == 2)
+                p2_pair_values<2>(T, &Gm[0][0], ce, pv);
+            else
+                p2_pair_values<3>(T, &Gm[0][0], ce, pv);
+            for (int p = 0; p < R.npairs; ++p) {
+                Ce[R.pj[p]][R.pl[p]] = Ce[R.pl[p]][R.pj[p]] = pv[p];
+                Ce[R.pj[p]][R.pj[p]] -= pv[p];
+                Ce[R.pl[p]][R.pl[p]] -= pv[p];
+            }
+        }
+        for (int j = 0; j < npe; ++j)
+            for (int l = 0; l < npe; ++l, ++k) {
+                if (rows) rows[k] = loc[t2.elem_nodes[(int64_t)e * npe + j]];
+                if (cols) cols[k] = loc[t2.elem_nodes[(int64_t)e * npe + l]];
+                if (M) M[k] = Me[j][l];
+                if (A) A[k] = Ae[j][l];
+                if (Ac) Ac[k] = Ce[j][l];
+            }
+    }
+}
+
 // Element stiffness matrices [n_elem][4][4] (elements in el_nodes order) and the node -> element
 // incidence, for the adjoint of the weighted stiffness A_r^{k}(c).
 void build_problem_stiffness(knp_problem* P, std::vector<double>& elA, std::vector<int32_t>& neptr,
@@ -539,3 +906,18 @@ void state_copy_in(knp_problem* p, bool device, const double* c_i, const double*
 }
 
 }  // namespace knp
+
+extern "C" knp_status knp_mesh_p2_region_matrices(const knp_mesh* mesh, int32_t region, const double* c,
+                                                  int64_t* count, int32_t* rows, int32_t* cols, double* M, double* A,
+                                                  double* Ac) {
+    return knp::guarded([&] {
+        KNP_REQUIRE(mesh && count, KNP_ERR_INVALID_ARG, "NULL argument");
+        KNP_REQUIRE(region == 0 || region == 1, KNP_ERR_INVALID_ARG, "region must be 0 or 1 (got %d)", region);
+        KNP_REQUIRE(!Ac || c, KNP_ERR_INVALID_ARG, "the weighted stiffness needs the coefficient c");
+        const int64_t npe = (int64_t)(mesh->dim + 1) * (mesh->dim + 2) / 2;
+        const int64_t ne = (int64_t)(region == 0 ? mesh->elems_i.size() : mesh->elems_e.size());
+        *count = ne * npe * npe;
+        if (rows || cols || M || A || Ac) knp::p2_region_triplets(*mesh, region, c, rows, cols, M, A, Ac);
+    });
+}
+

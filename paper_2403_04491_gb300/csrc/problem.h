@@ -104,6 +104,9 @@ struct knp_problem {
     int32_t dim = 0;
     int64_t N_i = 0, N_e = 0, n_nodes = 0, n_mv = 0, nf = 0, n_elem = 0, n_edges = 0, n_pairs = 0, n_edge_inc = 0;
     int32_t pin = -1;               // global node of the pinned phi_e
+    int32_t degree = 1;             // polynomial degree p of the Lagrange spaces (1 or 2)
+    int32_t npe = 0;                // nodes per element: d+1 (P1) or (d+1)(d+2)/2 (P2)
+    int32_t nfn = 0;                // nodes per membrane facet: d (P1) or d(d+1)/2 (P2)
     double t = 0.0;
     int64_t step_index = 0;
     bool assembled = false;
@@ -124,6 +127,9 @@ struct knp_problem {
     knp::DArray<int32_t> eptr, einc;     // edge -> incident elements (CSR)
     knp::DArray<double> ecoef;           // element stiffness entry a^T_jl per incidence
     knp::DArray<double> ak;              // [3][n_edges] weighted stiffness per edge
+    // P2 (degree 2): cbar holds [3][n_elem * n_pairs] element pair values of A_r^{k}, einc the
+    // (element, local pair) slot of each incidence and ecoef 1
+    knp::DArray<double> el_g;            // P2: [n_elem][16] |T| grad lambda_a . grad lambda_b
 
     // membrane data
     knp::DArray<int32_t> mv_g;           // [2][n_mv] global i-node and e-node of each membrane vertex
@@ -157,8 +163,11 @@ struct knp_problem {
 };
 
 namespace knp {
+// problem.cu
+void build_problem_p2(knp_problem* P);
 // assemble.cu
 void launch_assembly(knp_problem* p);
+void p2_upload_tables(cudaStream_t st);
 double stimulus_at(const knp_problem_desc& d, double t);
 // adjoint.cu
 void adjoint_free(AdjointWork* w);

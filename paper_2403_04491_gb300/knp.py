@@ -61,7 +61,7 @@ class ProblemDesc(C.Structure):
                 ("stim_a", C.c_double), ("stim_tau", C.c_double), ("stim_mask", C.POINTER(C.c_uint8)),
                 ("rho_pump", C.c_double), ("P_na", C.c_double), ("P_k", C.c_double),
                 ("source_i", C.POINTER(C.c_double)), ("source_e", C.POINTER(C.c_double)),
-                ("source_t0", C.c_double), ("source_t1", C.c_double)]
+                ("source_t0", C.c_double), ("source_t1", C.c_double), ("degree", C.c_int32)]
 
 
 class AmgOpts(C.Structure):
@@ -102,6 +102,7 @@ SIGNATURES = {
     "knp_mesh_destroy": [C.c_void_p],
     "knp_mesh_p2_get_info": [C.c_void_p, C.POINTER(P2Info)],
     "knp_mesh_p2_tables": [C.c_void_p, _IP, _IP, _IP, _IP, _IP, _IP, _IP],
+    "knp_mesh_p2_region_matrices": [C.c_void_p, C.c_int32, _DP, _LP, _IP, _IP, _DP, _DP, _DP],
     "knp_problem_create": [C.c_void_p, C.POINTER(ProblemDesc), C.c_void_p, C.POINTER(C.c_void_p)],
     "knp_problem_destroy": [C.c_void_p],
     "knp_sync": [C.c_void_p],
@@ -221,6 +222,24 @@ class Mesh:
         out.update(t)
         return out
 
+    def p2_region_matrices(self, region, c=None):
+        """knp_mesh_p2_region_matrices: the P2 M_r, A_r (and A_r^{c} for nodal c on the region's P2
+        nodes) of region 0 (i) or 1 (e) as scipy CSR matrices."""
+        import scipy.sparse as sp
+        cnt = C.c_int64()
+        cc = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+        _check(_lib.knp_mesh_p2_region_matrices(self.handle, int(region), _dptr(cc), C.byref(cnt), None, None, None,
+                                                None, None))
+        r = np.empty(cnt.value, np.int32)
+        col = np.empty(cnt.value, np.int32)
+        M, A = np.empty(cnt.value), np.empty(cnt.value)
+        Ac = None if cc is None else np.empty(cnt.value)
+        _check(_lib.knp_mesh_p2_region_matrices(self.handle, int(region), _dptr(cc), C.byref(cnt), _iptr(r),
+                                                _iptr(col), _dptr(M), _dptr(A), _dptr(Ac)))
+        n = self.p2()["N_i" if region == 0 else "N_e"]
+        mk = lambda v: sp.coo_matrix((v, (r, col)), shape=(n, n)).tocsr()
+        return (mk(M), mk(A)) if Ac is None else (mk(M), mk(A), mk(Ac))
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.knp_mesh_destroy(self.handle)
@@ -274,8 +293,12 @@ class Problem:
         d.rho_pump = float(desc.get("rho_pump", 1.115e-6))
         d.P_na = float(desc.get("P_na", 10.0))
         d.P_k = float(desc.get("P_k", 1.5))
-        # bulk source per vertex [n_vertices][n_ions] for the i and e copies (None = none)
-        nv = mesh.info["n_vertices"]
+        # polynomial degree (1: P1, 2: P2 on the nodes of Mesh.p2())
+        self.degree = int(desc.get("degree", 1))
+        d.degree = self.degree
+        p2 = mesh.p2() if self.degree == 2 else None
+        # bulk source per vertex (P1) or per global P2 node (P2), [n][n_ions], for the i and e copies
+        nv = mesh.info["n_vertices"] if p2 is None else p2["n_nodes"]
         self._source = {}
         for key in ("source_i", "source_e"):
             v = desc.get(key)
@@ -298,8 +321,12 @@ class Problem:
         _check(lib.knp_problem_create(mesh.handle, C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h)))
         self.handle = h
         self.n_ions = n_ions
-        self.N_i, self.N_e = mesh.info["N_i"], mesh.info["N_e"]
-        self.n_mv = mesh.info["n_membrane_vertices"]
+        if p2 is None:
+            self.N_i, self.N_e = mesh.info["N_i"], mesh.info["N_e"]
+            self.n_mv = mesh.info["n_membrane_vertices"]
+        else:
+            self.N_i, self.N_e = p2["N_i"], p2["N_e"]
+            self.n_mv = p2["n_membrane_nodes"]
         self.n_dof = 4 * (self.N_i + self.N_e)
 
     def sync(self):
@@ -481,18 +508,24 @@ def facet_arrays(cfg, mesh: Mesh):
     return model, gleak, mask
 
 
-def problem_from_config(cfg, stream=None, mesh: Mesh = None):
-    """Mesh and Problem for a synthetic workload description (``synth.Config``)."""
+def problem_from_config(cfg, stream=None, mesh: Mesh = None, degree: int = 1):
+    """Mesh and Problem for a synthetic workload description (``synth.Config``); degree 1 (P1) or 2
+    (P2 Lagrange elements, the bulk source evaluated at the P2 nodes)."""
     m = cfg.mesh
     if mesh is None:
         mesh = Mesh(m.coords, m.elems, m.elem_tag)
     p = cfg.params
     model, gleak, mask = facet_arrays(cfg, mesh)
+    if degree == 2:
+        e = mesh.p2()["edges"]
+        source_e = cfg.source_e_at(np.vstack([m.coords, 0.5 * (m.coords[e[:, 0]] + m.coords[e[:, 1]])]))
+    else:
+        source_e = cfg.vertex_source_e()
     desc = dict(n_ions=3, z=p["z"], D_i=p["D"], D_e=p["D"], R=p["R"], T=p["T"], F=p["F"], Cm=p["Cm"], dt=cfg.dt,
                 c_i0=p["c_i0"], c_e0=p["c_e0"], phi_M0=p["phi_M0"], facet_model=model, facet_gleak=gleak,
                 ion_na=0, ion_k=1, gbar_na=p["gbar_Na"], gbar_k=p["gbar_K"], phi_rest=p["phi_rest"],
                 w0=(p["n0"], p["m0"], p["h0"]), n_ode=25, stim_kind=cfg.stim_kind, stim_gbar=cfg.stim_gbar,
                 stim_t0=cfg.stim_t0, stim_t1=cfg.stim_t1, stim_a=cfg.stim_a, stim_tau=cfg.stim_tau,
                 stim_mask=mask, rho_pump=p["rho_pump"], P_na=p["P_Na"], P_k=p["P_K"],
-                source_e=cfg.vertex_source_e(), source_t0=cfg.source_t0, source_t1=cfg.source_t1)
+                source_e=source_e, source_t0=cfg.source_t0, source_t1=cfg.source_t1, degree=degree)
     return mesh, Problem(mesh, desc, stream=stream)

@@ -4,9 +4,10 @@ import numpy as np
 from oracle import problem as oproblem, solve as osolve, step as ostep, system as osystem
 
 
-def oracle_run(cfg, n_steps, exact="direct"):
-    """Oracle states u_0..u_n. exact='direct' (sparse LU of A) or 'lu_p0' (GMRES with LU(P_0) to 1e-14)."""
-    pb, s0 = oproblem.from_config(cfg)
+def oracle_run(cfg, n_steps, exact="direct", degree=1):
+    """Oracle states u_0..u_n. exact='direct' (sparse LU of A) or 'lu_p0' (GMRES with LU(P_0) to 1e-14);
+    degree 1 (P1) or 2 (P2)."""
+    pb, s0 = oproblem.from_config(cfg, degree=degree)
     kw = {}
     if exact == "lu_p0":
         kw = dict(method="gmres", M=osolve.lu_P0(osystem.preconditioner_P0(pb, s0)), rtol=1e-14)

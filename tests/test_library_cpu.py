@@ -210,3 +210,26 @@ def test_p2_nodes_match_oracle(lib, cfg, pin):
         assert T.pin_node >= m.coords.shape[0]      # this pin point sits nearest to an edge midpoint
     # a second query returns the same tables (built once)
     assert np.array_equal(M.p2()["elem_nodes"], P["elem_nodes"])
+
+
+@pytest.mark.parametrize("cfg", [make_config(1).with_nx(16), model_a(3, 4, 1e-4), make_config(8)],
+                         ids=["2d", "3d", "3d-iref"])
+def test_p2_region_matrices_match_oracle(lib, cfg):
+    """knp_mesh_p2_region_matrices: the library's P2 M_r and A_r (the static values of its P2
+    problems) and A_r^{c} for a random nodal c (the per-step kernel's element arithmetic) equal the
+    oracle's to rounding."""
+    from oracle import problem
+    from paper_2403_04491_gb300 import Mesh
+    m = cfg.mesh
+    M = Mesh(m.coords, m.elems, m.elem_tag)
+    pb, _ = problem.from_config(cfg, degree=2)
+    from oracle import p2
+    rng = np.random.default_rng(4)
+    for region, r in ((0, "i"), (1, "e")):
+        c = rng.uniform(1.0, 3.0, getattr(pb.topo, "N_" + r))
+        Mr, Ar, Acr = M.p2_region_matrices(region, c)
+        Ac_ref = p2.weighted_stiffness(pb.geo["cache_" + r], c, pb.geo["en_" + r], len(c))
+        for lib_mat, ref in ((Mr, pb.geo["M_" + r]), (Ar, pb.geo["A_" + r]), (Acr, Ac_ref)):
+            d = (lib_mat - ref).tocoo()
+            assert lib_mat.shape == ref.shape
+            assert (abs(d.data).max() if d.nnz else 0.0) <= 1e-13 * abs(ref).max()
