@@ -50,6 +50,9 @@ def parse():
                          "rtol 1e-8), 4 (16-cell 2D), 5 (512-cell 256^3, FP32 hierarchy, rtol 1e-8), "
                          "6 (Kir-Na/K 64^3 with a K bolus), 7 (Kir-Na/K 2D), 8 (3D HH, interface-refined grid)")
     ap.add_argument("--nx", type=int, default=None, help="override the mesh resolution of the workload")
+    ap.add_argument("--degree", type=int, default=1, choices=[1, 2],
+                    help="polynomial degree of the Lagrange elements (2: P2, Section 3.3; with --nx 32 the 3D "
+                         "workload has the node lattice of the 64^3 P1 one)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time a checkpointed forward + adjoint run of the 16-cell 2D workload (KNPFunction)")
     args = ap.parse_args()
@@ -60,10 +63,11 @@ def parse():
     return args
 
 
-def workload_name(cfg, n_dof):
+def workload_name(cfg, n_dof, degree=1):
     membrane = {0: "leak", 1: "HH", 2: "Kir-Na/K"}[cfg.model]
     src = "" if cfg.source_e is None else ", extracellular K bolus / Na removal for x < L/2, 0 < t <= 2 ms"
-    return (f"{cfg.name}: {cfg.dim}D, {cfg.nx}^{cfg.dim} mesh, {len(cfg.cell_lo)} cell(s), {n_dof:,} DOF, "
+    el = "" if degree == 1 else ", P2 elements"
+    return (f"{cfg.name}: {cfg.dim}D, {cfg.nx}^{cfg.dim} mesh{el}, {len(cfg.cell_lo)} cell(s), {n_dof:,} DOF, "
             f"dt {cfg.dt * 1e3:g} ms, {membrane} membrane{src}")
 
 
@@ -76,7 +80,7 @@ from synth import make_config
 from oracle import problem, solve, step, system
 cfg = make_config(2).with_nx({nx})
 t0 = time.perf_counter()
-pb, s = problem.from_config(cfg)
+pb, s = problem.from_config(cfg, degree={degree})
 M = solve.lu_P0(system.preconditioner_P0(pb, s))
 t_setup = time.perf_counter() - t0
 for _ in range({warmup}):
@@ -90,16 +94,17 @@ print(json.dumps(dict(n_dof=int(pb.topo.n_dof(3)), setup_s=t_setup, times=times)
 """
 
 
-def run_oracle(steps, warmup, nx=SAMPLE_NX):
+def run_oracle(steps, warmup, nx=SAMPLE_NX, degree=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, steps=steps, warmup=warmup)
+    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, steps=steps, warmup=warmup, degree=degree)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample_desc(nx, steps):
-    return (f"oracle (numpy/scipy FP64, 1 thread) on the same scenario at {nx}^3 (same cell, stimulus, dt); "
+def oracle_sample_desc(nx, steps, degree=1):
+    el = "" if degree == 1 else " with P2 elements"
+    return (f"oracle (numpy/scipy FP64, 1 thread) on the same scenario at {nx}^3{el} (same cell, stimulus, dt); "
             f"{steps} steps of assembly + GMRES(30) with LU(P_0) to 1e-13, after 1 untimed step")
 
 
@@ -310,7 +315,7 @@ def ours(args):
         cfg = cfg.with_nx(args.nx)
     prec = 0 if args.precision == "fp64" else 1
     t0 = time.perf_counter()
-    mesh, prob = problem_from_config(cfg)
+    mesh, prob = problem_from_config(cfg, degree=args.degree)
     t_create = time.perf_counter() - t0
     t0 = time.perf_counter()
     prob.amg_setup(precision=prec)
@@ -347,9 +352,10 @@ def ours(args):
     # end to end through the public API with host buffers: per step the state goes host->device,
     # one knp_step runs, and the new state comes back device->host (pinned host memory)
     e2e = None if args.no_e2e else e2e_run(prob, torch, args, n_dof, world)
-    mixed = None if (args.no_mixed or args.config != 2) else mixed_run(cfg, mesh, torch, args, n_dof)
+    mixed = None if (args.no_mixed or args.config != 2 or args.degree != 1) else mixed_run(cfg, mesh, torch, args,
+                                                                                            n_dof)
     report(args, prob, world, rank, ms, iters, launches, (prof, prof_spmv), clocks, e2e, mixed, n_dof, t_create, t_amg,
-           workload_name(cfg, n_dof), mem_gb)
+           workload_name(cfg, n_dof, args.degree), mem_gb)
 
 
 def e2e_run(prob, torch, args, n_dof, world):
@@ -465,9 +471,11 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
         mixed["speedup_fp32_rtol_1e-08_vs_plain_fp64_rtol_1e-10"] = mixed["rtol_1e-08"]["value"] / value
     cpu = None
     if not args.no_baseline and world == 1 and args.config == 2:
-        r = run_oracle(3, 1)
+        # P2: the sample's mesh is halved, so that its node lattice (and DOF) is the P1 sample's
+        snx = SAMPLE_NX if args.degree == 1 else SAMPLE_NX // 2
+        r = run_oracle(3, 1, nx=snx, degree=args.degree)
         v = r["n_dof"] * len(r["times"]) / sum(r["times"])
-        cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=oracle_sample_desc(SAMPLE_NX, 3))
+        cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=oracle_sample_desc(snx, 3, args.degree))
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64" if args.precision == "fp64" else "f64 (FGMRES) / f32 (AMG)", data="synthetic",
