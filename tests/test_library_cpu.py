@@ -233,3 +233,22 @@ def test_p2_region_matrices_match_oracle(lib, cfg):
             d = (lib_mat - ref).tocoo()
             assert lib_mat.shape == ref.shape
             assert (abs(d.data).max() if d.nnz else 0.0) <= 1e-13 * abs(ref).max()
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("cfg", [make_config(1).with_nx(16), make_config(7).with_nx(16), model_a(3, 4, 1e-4),
+                                 make_config(4).with_nx(64)], ids=["2d-leak", "2d-kir-source", "3d-hh", "2d-16cells"])
+def test_problem_host_build_reaches_the_device(lib, cfg, degree):
+    """knp_problem_create without a GPU: the whole host side of the problem build (pattern, static
+    values, incidences, membrane tables) runs, and the call stops at its first CUDA call with
+    KNP_ERR_CUDA, not at a host check. (On a machine with a GPU this test has nothing to check.)"""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2403_04491_gb300 import KnpError, problem_from_config
+    with pytest.raises(KnpError) as ei:
+        problem_from_config(cfg, degree=degree)
+    msg = str(ei.value)
+    assert ei.value.code == 4, msg
+    # the first device call of the build is an upload: cudaMalloc (P1) or the P2 tables' copy
+    assert "cudaMalloc" in msg or "cudaMemcpyToSymbol" in msg, msg
