@@ -252,3 +252,22 @@ def test_problem_host_build_reaches_the_device(lib, cfg, degree):
     assert ei.value.code == 4, msg
     # the first device call of the build is an upload: cudaMalloc (P1) or the P2 tables' copy
     assert "cudaMalloc" in msg or "cudaMemcpyToSymbol" in msg, msg
+
+
+def test_p2_arguments_are_checked(lib):
+    import ctypes as C
+    from paper_2403_04491_gb300 import KnpError, Mesh, problem_from_config
+    from paper_2403_04491_gb300 import knp
+    cfg = make_config(1).with_nx(8)
+    m = cfg.mesh
+    M = Mesh(m.coords, m.elems, m.elem_tag)
+    cnt = C.c_int64()
+    assert lib.knp_mesh_p2_region_matrices(M.handle, 2, None, C.byref(cnt), None, None, None, None, None) == 1
+    out = np.empty(1)
+    assert lib.knp_mesh_p2_region_matrices(M.handle, 0, None, C.byref(cnt), None, None, None, None,
+                                           out.ctypes.data_as(knp._DP)) == 1
+    assert lib.knp_mesh_p2_get_info(None, None) == 1
+    # an unknown degree is refused before any device work
+    with pytest.raises(KnpError) as ei:
+        problem_from_config(cfg, mesh=M, degree=3)
+    assert ei.value.code == 1 and "degree" in str(ei.value)
