@@ -1,8 +1,9 @@
 /* Plain C99 caller of the library's mesh intake (include/knp.h): reads a mesh from a binary
  * file (int32 dim; int64 n_vertices, n_elems; double coords[nv*dim]; int32 elems[ne*(dim+1)];
  * int32 tags[ne]; double pin[dim]), creates it through the C ABI, and prints the mesh info and
- * the membrane facets. Then it passes an out-of-range vertex id and prints the error code and
- * message. Used by tests/test_c_abi.py. */
+ * the membrane facets, the P2 node counts and the total of the intracellular P2 mass matrix. Then
+ * it passes an out-of-range vertex id and prints the error code and message. Used by
+ * tests/test_c_abi.py. */
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -49,6 +50,20 @@ int main(int argc, char** argv) {
         for (int j = 0; j < dim; ++j) printf(" %d", fv[k * dim + j]);
         printf(" %d %d %d\n", fe[k], fo[k], fc[k]);
     }
+    /* P2 nodes (Section 3.3, p = 2) and the summed mass of the intracellular P2 elements */
+    knp_p2_info p2;
+    if (knp_mesh_p2_get_info(mesh, &p2) != KNP_OK) return 1;
+    printf("p2 %lld %lld %lld %lld %lld %lld %lld\n", (long long)p2.n_edges, (long long)p2.n_nodes,
+           (long long)p2.N_i, (long long)p2.N_e, (long long)p2.n_membrane_nodes, (long long)p2.pin_node,
+           (long long)p2.n_dof);
+    int64_t cnt = 0;
+    if (knp_mesh_p2_region_matrices(mesh, 0, NULL, &cnt, NULL, NULL, NULL, NULL, NULL) != KNP_OK) return 1;
+    double* mv = malloc(sizeof(double) * (size_t)cnt);
+    if (knp_mesh_p2_region_matrices(mesh, 0, NULL, &cnt, NULL, NULL, mv, NULL, NULL) != KNP_OK) return 1;
+    double vol = 0.0;
+    for (int64_t k = 0; k < cnt; ++k) vol += mv[k];
+    printf("p2mass %lld %.17g\n", (long long)cnt, vol);
+    free(mv);
     knp_mesh_destroy(mesh);
 
     elems[0] = (int32_t)nv;   /* out of range */
