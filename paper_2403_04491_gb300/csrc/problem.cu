@@ -141,58 +141,33 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-void build_problem(knp_problem* P) {
-    const knp_mesh& m = *P->mesh;
-    const int dim = m.dim, nvpe = dim + 1;
-    const int64_t Ni = (int64_t)m.nodes_i.size(), Ne = (int64_t)m.nodes_e.size();
-    const int64_t n = Ni + Ne;
-    P->dim = dim;
-    P->N_i = Ni;
-    P->N_e = Ne;
-    P->n_nodes = n;
-    P->n_mv = (int64_t)m.mverts.size();
-    P->nf = m.nf();
-    P->n_elem = m.ne;
-    P->pin = (int32_t)(Ni + m.loc_e[m.pin_vertex]);
-    cudaStream_t st = P->stream;
+namespace {
 
-    // ---- elements with global node ids (intracellular first, then extracellular)
-    std::vector<int32_t> eln((size_t)m.ne * nvpe);
-    std::vector<int32_t> elem_src(m.ne);
-    {
-        int64_t k = 0;
-        for (int32_t e : m.elems_i) {
-            for (int j = 0; j < nvpe; ++j) eln[k * nvpe + j] = m.loc_i[m.elems[(int64_t)e * nvpe + j]];
-            elem_src[k++] = e;
-        }
-        for (int32_t e : m.elems_e) {
-            for (int j = 0; j < nvpe; ++j) eln[k * nvpe + j] = (int32_t)(Ni + m.loc_e[m.elems[(int64_t)e * nvpe + j]]);
-            elem_src[k++] = e;
-        }
-    }
-    // ---- node -> element incidence, then sorted neighbour lists per row
+// The region-internal pattern: node -> element incidence, sorted neighbour lists per row, the
+// sliced-ELL layout (padding points at its own row), and the undirected entry id of every
+// directed entry (-1 diagonal, -2 padding). eln holds npe global node ids per element.
+int64_t build_pattern(const std::vector<int32_t>& eln, int npe, int64_t ne, int64_t n, SellPattern& S,
+                      std::vector<int32_t>& row_len, std::vector<int32_t>& h_edge) {
     std::vector<int64_t> ne_ptr(n + 1, 0);
-    for (int64_t e = 0; e < m.ne; ++e)
-        for (int j = 0; j < nvpe; ++j) ne_ptr[eln[e * nvpe + j] + 1]++;
+    for (int64_t e = 0; e < ne; ++e)
+        for (int j = 0; j < npe; ++j) ne_ptr[eln[e * npe + j] + 1]++;
     for (int64_t i = 0; i < n; ++i) ne_ptr[i + 1] += ne_ptr[i];
     std::vector<int32_t> ne_list(ne_ptr[n]);
     {
         std::vector<int64_t> fill(ne_ptr.begin(), ne_ptr.end() - 1);
-        for (int64_t e = 0; e < m.ne; ++e)
-            for (int j = 0; j < nvpe; ++j) ne_list[fill[eln[e * nvpe + j]]++] = (int32_t)e;
+        for (int64_t e = 0; e < ne; ++e)
+            for (int j = 0; j < npe; ++j) ne_list[fill[eln[e * npe + j]]++] = (int32_t)e;
     }
-    std::vector<int32_t> row_len(n);
+    row_len.assign(n, 0);
     std::vector<std::vector<int32_t>> rows(n);
     for (int64_t r = 0; r < n; ++r) {
         auto& v = rows[r];
         for (int64_t t = ne_ptr[r]; t < ne_ptr[r + 1]; ++t)
-            for (int j = 0; j < nvpe; ++j) v.push_back(eln[(int64_t)ne_list[t] * nvpe + j]);
+            for (int j = 0; j < npe; ++j) v.push_back(eln[(int64_t)ne_list[t] * npe + j]);
         std::sort(v.begin(), v.end());
         v.erase(std::unique(v.begin(), v.end()), v.end());
         row_len[r] = (int32_t)v.size();
     }
-    // ---- sliced ELL
-    SellPattern& S = P->sell;
     S.n_rows = n;
     S.n_slices = (n + SELL_C - 1) / SELL_C;
     S.h_slice_ptr.assign(S.n_slices + 1, 0);
@@ -202,23 +177,19 @@ void build_problem(knp_problem* P) {
         S.h_slice_ptr[s + 1] = S.h_slice_ptr[s] + (int64_t)w * SELL_C;
     }
     S.n_entries = S.h_slice_ptr[S.n_slices];
+    KNP_REQUIRE(S.n_entries < INT32_MAX, KNP_ERR_INVALID_ARG, "pattern too large for 32-bit positions");
     S.h_col.assign(S.n_entries, 0);
-    std::vector<int32_t> h_edge(S.n_entries, -2);
+    h_edge.assign(S.n_entries, -2);
     for (int64_t s = 0; s < S.n_slices; ++s) {
         int64_t w = (S.h_slice_ptr[s + 1] - S.h_slice_ptr[s]) / SELL_C;
         for (int64_t lane = 0; lane < SELL_C; ++lane) {
             int64_t r = s * SELL_C + lane;
             for (int64_t k = 0; k < w; ++k) {
                 int64_t pos = S.h_slice_ptr[s] + k * SELL_C + lane;
-                if (r < n && k < row_len[r]) {
-                    S.h_col[pos] = rows[r][k];
-                } else {
-                    S.h_col[pos] = (int32_t)std::min<int64_t>(r, n - 1);  // padding: own row, zero values
-                }
+                S.h_col[pos] = (r < n && k < row_len[r]) ? rows[r][k] : (int32_t)std::min<int64_t>(r, n - 1);
             }
         }
     }
-    // ---- undirected edges j < l and their ids on both directed entries
     int64_t n_edges = 0;
     for (int64_t r = 0; r < n; ++r)
         for (int32_t k = 0; k < row_len[r]; ++k) {
@@ -237,9 +208,231 @@ void build_problem(knp_problem* P) {
                 h_edge[pos] = h_edge[sell_find(S, row_len, c, (int32_t)r)];
             }
         }
+    return n_edges;
+}
+
+// Membrane tables on the host: the region nodes of each membrane node, the facet node ->
+// membrane node map, facet areas, node -> (facet, slot) and pair -> (facet, slot, slot)
+// incidences (slots packed with `bits` bits each), and the cross-region CSR with its transpose.
+struct MembraneHost {
+    std::vector<int32_t> mvg, fmv, mvf_ptr, mvf, mp_ptr, mpf, tgt, xtp, xtr, xti;
+    std::vector<double> farea;
+    int64_t npairs = 0;
+};
+
+void build_membrane(knp_problem* P, const SellPattern& S, const std::vector<int32_t>& row_len,
+                    const std::vector<int32_t>& fnodes, int nfn, const std::vector<int32_t>& mnodes,
+                    const std::vector<int32_t>& loc_i, const std::vector<int32_t>& loc_e, int bits, MembraneHost& M) {
+    const knp_mesh& m = *P->mesh;
+    const int dim = m.dim;
+    const int64_t n = P->n_nodes, Ni = P->N_i, nmv = (int64_t)mnodes.size(), nf = m.nf();
+    M.mvg.resize(2 * nmv);
+    for (int64_t a = 0; a < nmv; ++a) {
+        int32_t x = mnodes[a];
+        M.mvg[a] = loc_i[x];
+        M.mvg[nmv + a] = (int32_t)(Ni + loc_e[x]);
+    }
+    M.fmv.resize(nf * nfn);
+    M.farea.resize(nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        for (int s = 0; s < nfn; ++s) {
+            int32_t x = fnodes[f * nfn + s];
+            M.fmv[f * nfn + s] = (int32_t)(std::lower_bound(mnodes.begin(), mnodes.end(), x) - mnodes.begin());
+        }
+        M.farea[f] = facet_area(m.coords.data(), dim, &m.facets[f * dim]);
+    }
+    M.mvf_ptr.assign(nmv + 1, 0);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int s = 0; s < nfn; ++s) M.mvf_ptr[M.fmv[f * nfn + s] + 1]++;
+    for (int64_t a = 0; a < nmv; ++a) M.mvf_ptr[a + 1] += M.mvf_ptr[a];
+    M.mvf.resize(M.mvf_ptr[nmv]);
+    {
+        std::vector<int32_t> fill(M.mvf_ptr.begin(), M.mvf_ptr.end() - 1);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int s = 0; s < nfn; ++s) M.mvf[fill[M.fmv[f * nfn + s]]++] = (int32_t)((f << bits) | s);
+    }
+    // membrane node pairs (a, b) sharing a facet, with the shared facets
+    struct PairInc {
+        int64_t key;
+        int32_t packed;
+    };
+    std::vector<PairInc> pinc;
+    pinc.reserve(nf * nfn * nfn);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int sa = 0; sa < nfn; ++sa)
+            for (int sb = 0; sb < nfn; ++sb) {
+                int64_t a = M.fmv[f * nfn + sa], b = M.fmv[f * nfn + sb];
+                pinc.push_back({a * nmv + b, (int32_t)((f << (2 * bits)) | (sa << bits) | sb)});
+            }
+    std::sort(pinc.begin(), pinc.end(), [](const PairInc& x, const PairInc& y) {
+        return x.key < y.key || (x.key == y.key && x.packed < y.packed);
+    });
+    std::vector<int64_t> pair_key;
+    M.mp_ptr.assign(1, 0);
+    M.mpf.clear();
+    for (size_t i = 0; i < pinc.size(); ++i) {
+        if (i == 0 || pinc[i].key != pinc[i - 1].key) {
+            pair_key.push_back(pinc[i].key);
+            M.mp_ptr.push_back(M.mp_ptr.back());
+        }
+        M.mpf.push_back(pinc[i].packed);
+        M.mp_ptr.back()++;
+    }
+    const int64_t npairs = (int64_t)pair_key.size();
+    M.npairs = npairs;
+    // cross-region CSR: row gi(a) -> col ge(b) and row ge(a) -> col gi(b)
+    std::vector<int32_t>& xp = P->h_xptr;
+    std::vector<int32_t>& xc = P->h_xcol;
+    xp.assign(n + 1, 0);
+    for (int64_t t = 0; t < npairs; ++t) {
+        int64_t a = pair_key[t] / nmv;
+        xp[M.mvg[a] + 1]++;
+        xp[M.mvg[nmv + a] + 1]++;
+    }
+    for (int64_t r = 0; r < n; ++r) xp[r + 1] += xp[r];
+    xc.assign(xp[n], 0);
+    M.tgt.resize(4 * npairs);
+    {
+        std::vector<int32_t> fill(xp.begin(), xp.end() - 1);
+        // pairs are sorted by (a, b), so columns within a row come out sorted by b
+        for (int64_t t = 0; t < npairs; ++t) {
+            int64_t a = pair_key[t] / nmv, b = pair_key[t] % nmv;
+            int32_t gia = M.mvg[a], gea = M.mvg[nmv + a], gib = M.mvg[b], geb = M.mvg[nmv + b];
+            M.tgt[4 * t + 0] = (int32_t)sell_find(S, row_len, gia, gib);
+            M.tgt[4 * t + 1] = (int32_t)sell_find(S, row_len, gea, geb);
+            KNP_REQUIRE(M.tgt[4 * t] >= 0 && M.tgt[4 * t + 1] >= 0, KNP_ERR_INVALID_MESH,
+                        "membrane facet node pair missing from the region pattern");
+            xc[fill[gia]] = geb;
+            M.tgt[4 * t + 2] = fill[gia]++;
+            xc[fill[gea]] = gib;
+            M.tgt[4 * t + 3] = fill[gea]++;
+        }
+    }
+    // transposed cross-region list (used by the transposed operator)
+    M.xtp.assign(n + 1, 0);
+    M.xtr.resize(xc.size());
+    M.xti.resize(xc.size());
+    for (size_t t = 0; t < xc.size(); ++t) M.xtp[xc[t] + 1]++;
+    for (int64_t r = 0; r < n; ++r) M.xtp[r + 1] += M.xtp[r];
+    {
+        std::vector<int32_t> fill(M.xtp.begin(), M.xtp.end() - 1);
+        for (int64_t r = 0; r < n; ++r)
+            for (int32_t t = xp[r]; t < xp[r + 1]; ++t) {
+                int32_t q = fill[xc[t]]++;
+                M.xtr[q] = (int32_t)r;
+                M.xti[q] = t;
+            }
+    }
+}
+
+// Uploads of the operator, assembly and membrane tables, the bulk source at the region nodes
+// (source_v indexed by the ids in nodes_i / nodes_e), the state vectors and u_0, w_0.
+void upload_problem(knp_problem* P, const std::vector<int32_t>& h_edge, const std::vector<double>& hm,
+                    const std::vector<double>& ha, const std::vector<int32_t>& eln, const std::vector<double>* hg,
+                    int64_t cbar_len, const std::vector<int32_t>& e_cnt, const std::vector<int32_t>& h_einc,
+                    const std::vector<double>& h_ecoef, const MembraneHost& M, const std::vector<int32_t>& nodes_i,
+                    const std::vector<int32_t>& nodes_e) {
+    cudaStream_t st = P->stream;
+    SellPattern& S = P->sell;
+    const int64_t n = P->n_nodes, Ni = P->N_i, nmv = P->n_mv;
+    S.slice_ptr.upload(S.h_slice_ptr, st);
+    S.col.upload(S.h_col, st);
+    P->sell_edge.upload(h_edge, st);
+    P->sell_m.upload(hm, st);
+    P->sell_a.upload(ha, st);
+    P->sell_e.alloc(3 * S.n_entries);
+    P->sell_e.zero(st);
+    P->xptr.upload(P->h_xptr, st);
+    P->xcol.upload(P->h_xcol, st);
+    P->xtptr.upload(M.xtp, st);
+    P->xtrow.upload(M.xtr, st);
+    P->xtidx.upload(M.xti, st);
+    P->xe.alloc(std::max<int64_t>(1, 3 * (int64_t)P->h_xcol.size()));
+    P->xe.zero(st);
+    P->el_nodes.upload(eln, st);
+    if (hg) P->el_g.upload(*hg, st);
+    P->cbar.alloc(cbar_len);
+    P->eptr.upload(e_cnt, st);
+    P->einc.upload(h_einc, st);
+    P->ecoef.upload(h_ecoef, st);
+    P->ak.alloc(std::max<int64_t>(1, 3 * P->n_edges));
+    P->mv_g.upload(M.mvg, st);
+    P->gates.alloc(3 * nmv);
+    P->gates_new.alloc(3 * nmv);
+    P->mfield.alloc(14 * nmv);
+    P->f_mv.upload(M.fmv, st);
+    P->f_area.upload(M.farea, st);
+    P->f_model.upload(P->facet_model, st);
+    P->f_gleak.upload(P->facet_gleak, st);
+    P->f_mask.upload(P->stim_mask, st);
+    P->mvf_ptr.upload(M.mvf_ptr, st);
+    P->mvf.upload(M.mvf, st);
+    P->mp_ptr.upload(M.mp_ptr, st);
+    P->mpf.upload(M.mpf, st);
+    P->mp_tgt.upload(M.tgt, st);
+    if (!P->source_v[0].empty() || !P->source_v[1].empty()) {
+        // bulk source at the nodes: the intracellular values for i-nodes, the extracellular ones for e-nodes
+        std::vector<double> hs(4 * n, 0.0);
+        for (int r = 0; r < 2; ++r) {
+            if (P->source_v[r].empty()) continue;
+            const std::vector<int32_t>& ids = r == 0 ? nodes_i : nodes_e;
+            const int64_t off = r == 0 ? 0 : Ni;
+            for (size_t j = 0; j < ids.size(); ++j)
+                for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)ids[j] * KI + k];
+        }
+        P->src.upload(hs, st);
+    }
+    P->u.alloc(4 * n);
+    P->f.alloc(4 * n);
+    P->f.zero(st);
+    P->sinv.alloc(4 * n);
+    P->svec.alloc(4 * n);
+    P->swt.alloc(4 * n);
+    const knp_problem_desc& d = P->desc;
+    count_launch(nmv ? 2 : 1);
+    k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
+                                          d.c_e0[2], d.phi_M0);
+    if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
+    KNP_CUDA(cudaGetLastError());
+    KNP_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+void build_problem(knp_problem* P) {
+    const knp_mesh& m = *P->mesh;
+    const int dim = m.dim, nvpe = dim + 1;
+    const int64_t Ni = (int64_t)m.nodes_i.size(), Ne = (int64_t)m.nodes_e.size();
+    const int64_t n = Ni + Ne;
+    P->dim = dim;
+    P->npe = nvpe;
+    P->nfn = dim;
+    P->N_i = Ni;
+    P->N_e = Ne;
+    P->n_nodes = n;
+    P->n_mv = (int64_t)m.mverts.size();
+    P->nf = m.nf();
+    P->n_elem = m.ne;
+    P->pin = (int32_t)(Ni + m.loc_e[m.pin_vertex]);
+
+    // ---- elements with global node ids (intracellular first, then extracellular)
+    std::vector<int32_t> eln((size_t)m.ne * nvpe);
+    std::vector<int32_t> elem_src(m.ne);
+    {
+        int64_t k = 0;
+        for (int32_t e : m.elems_i) {
+            for (int j = 0; j < nvpe; ++j) eln[k * nvpe + j] = m.loc_i[m.elems[(int64_t)e * nvpe + j]];
+            elem_src[k++] = e;
+        }
+        for (int32_t e : m.elems_e) {
+            for (int j = 0; j < nvpe; ++j) eln[k * nvpe + j] = (int32_t)(Ni + m.loc_e[m.elems[(int64_t)e * nvpe + j]]);
+            elem_src[k++] = e;
+        }
+    }
+    SellPattern& S = P->sell;
+    std::vector<int32_t> row_len, h_edge;
+    const int64_t n_edges = build_pattern(eln, nvpe, m.ne, n, S, row_len, h_edge);
     P->n_edges = n_edges;
-    rows.clear();
-    rows.shrink_to_fit();
     // ---- static M and A, and the edge incidence (element, a^T_jl)
     std::vector<double> hm(S.n_entries, 0.0), ha(S.n_entries, 0.0);
     std::vector<int32_t> e_cnt(n_edges + 1, 0);
@@ -286,165 +479,11 @@ void build_problem(knp_problem* P) {
                     fill[id]++;
                 }
     }
-    // ---- membrane
-    const int64_t nmv = P->n_mv, nf = P->nf;
-    std::vector<int32_t> h_mvg(2 * nmv);
-    for (int64_t a = 0; a < nmv; ++a) {
-        int32_t v = m.mverts[a];
-        h_mvg[a] = m.loc_i[v];
-        h_mvg[nmv + a] = (int32_t)(Ni + m.loc_e[v]);
-    }
-    std::vector<int32_t> h_fmv(nf * dim);
-    std::vector<double> h_farea(nf);
-    for (int64_t f = 0; f < nf; ++f) {
-        for (int d = 0; d < dim; ++d) {
-            int32_t v = m.facets[f * dim + d];
-            h_fmv[f * dim + d] = (int32_t)(std::lower_bound(m.mverts.begin(), m.mverts.end(), v) - m.mverts.begin());
-        }
-        h_farea[f] = facet_area(m.coords.data(), dim, &m.facets[f * dim]);
-    }
-    std::vector<int32_t> h_mvf_ptr(nmv + 1, 0);
-    for (int64_t f = 0; f < nf; ++f)
-        for (int d = 0; d < dim; ++d) h_mvf_ptr[h_fmv[f * dim + d] + 1]++;
-    for (int64_t a = 0; a < nmv; ++a) h_mvf_ptr[a + 1] += h_mvf_ptr[a];
-    std::vector<int32_t> h_mvf(h_mvf_ptr[nmv]);
-    {
-        std::vector<int32_t> fill(h_mvf_ptr.begin(), h_mvf_ptr.end() - 1);
-        for (int64_t f = 0; f < nf; ++f)
-            for (int d = 0; d < dim; ++d) h_mvf[fill[h_fmv[f * dim + d]]++] = (int32_t)((f << 2) | d);
-    }
-    // membrane vertex pairs (a, b) sharing a facet, with the shared facets
-    struct PairInc {
-        int64_t key;
-        int32_t packed;
-    };
-    std::vector<PairInc> pinc;
-    pinc.reserve(nf * dim * dim);
-    for (int64_t f = 0; f < nf; ++f)
-        for (int sa = 0; sa < dim; ++sa)
-            for (int sb = 0; sb < dim; ++sb) {
-                int64_t a = h_fmv[f * dim + sa], b = h_fmv[f * dim + sb];
-                pinc.push_back({a * nmv + b, (int32_t)((f << 4) | (sa << 2) | sb)});
-            }
-    std::sort(pinc.begin(), pinc.end(), [](const PairInc& x, const PairInc& y) {
-        return x.key < y.key || (x.key == y.key && x.packed < y.packed);
-    });
-    std::vector<int64_t> pair_key;
-    std::vector<int32_t> h_mp_ptr(1, 0), h_mpf;
-    for (size_t i = 0; i < pinc.size(); ++i) {
-        if (i == 0 || pinc[i].key != pinc[i - 1].key) {
-            pair_key.push_back(pinc[i].key);
-            h_mp_ptr.push_back(h_mp_ptr.back());
-        }
-        h_mpf.push_back(pinc[i].packed);
-        h_mp_ptr.back()++;
-    }
-    const int64_t npairs = (int64_t)pair_key.size();
-    P->n_pairs = npairs;
-    // cross-region CSR: row gi(a) -> col ge(b) and row ge(a) -> col gi(b)
-    std::vector<int32_t>& xp = P->h_xptr;
-    std::vector<int32_t>& xc = P->h_xcol;
-    xp.assign(n + 1, 0);
-    for (int64_t t = 0; t < npairs; ++t) {
-        int64_t a = pair_key[t] / nmv;
-        xp[h_mvg[a] + 1]++;
-        xp[h_mvg[nmv + a] + 1]++;
-    }
-    for (int64_t r = 0; r < n; ++r) xp[r + 1] += xp[r];
-    xc.assign(xp[n], 0);
-    std::vector<int32_t> h_tgt(4 * npairs);
-    {
-        std::vector<int32_t> fill(xp.begin(), xp.end() - 1);
-        // pairs are sorted by (a, b), so columns within a row come out sorted by b
-        for (int64_t t = 0; t < npairs; ++t) {
-            int64_t a = pair_key[t] / nmv, b = pair_key[t] % nmv;
-            int32_t gia = h_mvg[a], gea = h_mvg[nmv + a], gib = h_mvg[b], geb = h_mvg[nmv + b];
-            h_tgt[4 * t + 0] = (int32_t)sell_find(S, row_len, gia, gib);
-            h_tgt[4 * t + 1] = (int32_t)sell_find(S, row_len, gea, geb);
-            KNP_REQUIRE(h_tgt[4 * t] >= 0 && h_tgt[4 * t + 1] >= 0, KNP_ERR_INVALID_MESH,
-                        "membrane facet edge missing from the region pattern");
-            xc[fill[gia]] = geb;
-            h_tgt[4 * t + 2] = fill[gia]++;
-            xc[fill[gea]] = gib;
-            h_tgt[4 * t + 3] = fill[gea]++;
-        }
-    }
-    KNP_REQUIRE(S.n_entries < INT32_MAX, KNP_ERR_INVALID_ARG, "pattern too large for 32-bit positions");
-    // transposed cross-region list (used by the transposed operator)
-    std::vector<int32_t> xtp(n + 1, 0), xtr(xc.size()), xti(xc.size());
-    for (size_t t = 0; t < xc.size(); ++t) xtp[xc[t] + 1]++;
-    for (int64_t r = 0; r < n; ++r) xtp[r + 1] += xtp[r];
-    {
-        std::vector<int32_t> fill(xtp.begin(), xtp.end() - 1);
-        for (int64_t r = 0; r < n; ++r)
-            for (int32_t t = xp[r]; t < xp[r + 1]; ++t) {
-                int32_t q = fill[xc[t]]++;
-                xtr[q] = (int32_t)r;
-                xti[q] = t;
-            }
-    }
-
-    // ---- uploads
-    S.slice_ptr.upload(S.h_slice_ptr, st);
-    S.col.upload(S.h_col, st);
-    P->sell_edge.upload(h_edge, st);
-    P->sell_m.upload(hm, st);
-    P->sell_a.upload(ha, st);
-    P->sell_e.alloc(3 * S.n_entries);
-    P->sell_e.zero(st);
-    P->xptr.upload(xp, st);
-    P->xcol.upload(xc, st);
-    P->xtptr.upload(xtp, st);
-    P->xtrow.upload(xtr, st);
-    P->xtidx.upload(xti, st);
-    P->xe.alloc(std::max<int64_t>(1, 3 * (int64_t)xc.size()));
-    P->xe.zero(st);
-    P->el_nodes.upload(eln, st);
-    P->cbar.alloc(3 * m.ne);
-    P->eptr.upload(e_cnt, st);
-    P->einc.upload(h_einc, st);
-    P->ecoef.upload(h_ecoef, st);
-    P->ak.alloc(std::max<int64_t>(1, 3 * n_edges));
-    P->mv_g.upload(h_mvg, st);
-    P->gates.alloc(3 * nmv);
-    P->gates_new.alloc(3 * nmv);
-    P->mfield.alloc(14 * nmv);
-    P->f_mv.upload(h_fmv, st);
-    P->f_area.upload(h_farea, st);
-    P->f_model.upload(P->facet_model, st);
-    P->f_gleak.upload(P->facet_gleak, st);
-    P->f_mask.upload(P->stim_mask, st);
-    P->mvf_ptr.upload(h_mvf_ptr, st);
-    P->mvf.upload(h_mvf, st);
-    P->mp_ptr.upload(h_mp_ptr, st);
-    P->mpf.upload(h_mpf, st);
-    P->mp_tgt.upload(h_tgt, st);
-    if (!P->source_v[0].empty() || !P->source_v[1].empty()) {
-        // bulk source at the nodes: the vertex's intracellular values for i-nodes, its
-        // extracellular values for e-nodes
-        std::vector<double> hs(4 * n, 0.0);
-        for (int r = 0; r < 2; ++r) {
-            if (P->source_v[r].empty()) continue;
-            const std::vector<int32_t>& verts = r == 0 ? m.nodes_i : m.nodes_e;
-            const int64_t off = r == 0 ? 0 : Ni;
-            for (size_t j = 0; j < verts.size(); ++j)
-                for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)verts[j] * KI + k];
-        }
-        P->src.upload(hs, st);
-    }
-    P->u.alloc(4 * n);
-    P->f.alloc(4 * n);
-    P->f.zero(st);
-    P->sinv.alloc(4 * n);
-    P->svec.alloc(4 * n);
-    P->swt.alloc(4 * n);
-    const knp_problem_desc& d = P->desc;
-    count_launch(nmv ? 2 : 1);
-    k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
-                                          d.c_e0[2], d.phi_M0);
-    if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
-    KNP_CUDA(cudaGetLastError());
-    KNP_CUDA(cudaStreamSynchronize(st));
+    // ---- membrane (P1: the facet's vertices are its nodes)
+    MembraneHost M;
+    build_membrane(P, S, row_len, m.facets, dim, m.mverts, m.loc_i, m.loc_e, 2, M);
+    P->n_pairs = M.npairs;
+    upload_problem(P, h_edge, hm, ha, eln, nullptr, 3 * m.ne, e_cnt, h_einc, h_ecoef, M, m.nodes_i, m.nodes_e);
 }
 
 // ---- P2 elements (Section 3.3 with p = 2) ---------------------------------------------------
@@ -500,7 +539,6 @@ void build_problem_p2(knp_problem* P) {
     P->pin = (int32_t)(Ni + t2.loc_e[t2.pin_node]);
     KNP_REQUIRE(m.ne * npairs < INT32_MAX, KNP_ERR_INVALID_ARG, "too many P2 element pairs for 32-bit slots");
     KNP_REQUIRE(P->nf < (1 << 25), KNP_ERR_INVALID_ARG, "too many membrane facets for the P2 tables");
-    cudaStream_t st = P->stream;
 
     // ---- elements with global node ids (intracellular first, then extracellular)
     std::vector<int32_t> eln((size_t)m.ne * npe);
@@ -517,73 +555,10 @@ void build_problem_p2(knp_problem* P) {
             elem_src[k++] = e;
         }
     }
-    // ---- node -> element incidence, then sorted neighbour lists per row
-    std::vector<int64_t> ne_ptr(n + 1, 0);
-    for (int64_t e = 0; e < m.ne; ++e)
-        for (int j = 0; j < npe; ++j) ne_ptr[eln[e * npe + j] + 1]++;
-    for (int64_t i = 0; i < n; ++i) ne_ptr[i + 1] += ne_ptr[i];
-    std::vector<int32_t> ne_list(ne_ptr[n]);
-    {
-        std::vector<int64_t> fill(ne_ptr.begin(), ne_ptr.end() - 1);
-        for (int64_t e = 0; e < m.ne; ++e)
-            for (int j = 0; j < npe; ++j) ne_list[fill[eln[e * npe + j]]++] = (int32_t)e;
-    }
-    std::vector<int32_t> row_len(n);
-    std::vector<std::vector<int32_t>> rows(n);
-    for (int64_t r = 0; r < n; ++r) {
-        auto& v = rows[r];
-        for (int64_t q = ne_ptr[r]; q < ne_ptr[r + 1]; ++q)
-            for (int j = 0; j < npe; ++j) v.push_back(eln[(int64_t)ne_list[q] * npe + j]);
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
-        row_len[r] = (int32_t)v.size();
-    }
-    // ---- sliced ELL
     SellPattern& S = P->sell;
-    S.n_rows = n;
-    S.n_slices = (n + SELL_C - 1) / SELL_C;
-    S.h_slice_ptr.assign(S.n_slices + 1, 0);
-    for (int64_t s = 0; s < S.n_slices; ++s) {
-        int32_t w = 0;
-        for (int64_t r = s * SELL_C; r < std::min<int64_t>(n, (s + 1) * SELL_C); ++r) w = std::max(w, row_len[r]);
-        S.h_slice_ptr[s + 1] = S.h_slice_ptr[s] + (int64_t)w * SELL_C;
-    }
-    S.n_entries = S.h_slice_ptr[S.n_slices];
-    KNP_REQUIRE(S.n_entries < INT32_MAX, KNP_ERR_INVALID_ARG, "pattern too large for 32-bit positions");
-    S.h_col.assign(S.n_entries, 0);
-    std::vector<int32_t> h_edge(S.n_entries, -2);
-    for (int64_t s = 0; s < S.n_slices; ++s) {
-        int64_t w = (S.h_slice_ptr[s + 1] - S.h_slice_ptr[s]) / SELL_C;
-        for (int64_t lane = 0; lane < SELL_C; ++lane) {
-            int64_t r = s * SELL_C + lane;
-            for (int64_t k = 0; k < w; ++k) {
-                int64_t pos = S.h_slice_ptr[s] + k * SELL_C + lane;
-                S.h_col[pos] = (r < n && k < row_len[r]) ? rows[r][k] : (int32_t)std::min<int64_t>(r, n - 1);
-            }
-        }
-    }
-    // ---- undirected entries j < l and their ids on both directed entries
-    int64_t n_edges = 0;
-    for (int64_t r = 0; r < n; ++r)
-        for (int32_t k = 0; k < row_len[r]; ++k) {
-            int32_t c = rows[r][k];
-            int64_t pos = S.h_slice_ptr[r / SELL_C] + (int64_t)k * SELL_C + r % SELL_C;
-            if (c == r)
-                h_edge[pos] = -1;
-            else if (c > r)
-                h_edge[pos] = (int32_t)n_edges++;
-        }
-    for (int64_t r = 0; r < n; ++r)
-        for (int32_t k = 0; k < row_len[r]; ++k) {
-            int32_t c = rows[r][k];
-            if (c < r) {
-                int64_t pos = S.h_slice_ptr[r / SELL_C] + (int64_t)k * SELL_C + r % SELL_C;
-                h_edge[pos] = h_edge[sell_find(S, row_len, c, (int32_t)r)];
-            }
-        }
+    std::vector<int32_t> row_len, h_edge;
+    const int64_t n_edges = build_pattern(eln, npe, m.ne, n, S, row_len, h_edge);
     P->n_edges = n_edges;
-    rows.clear();
-    rows.shrink_to_fit();
     // ---- static M and A; |T| G per element; the (element, pair) incidences of each undirected entry
     std::vector<double> hm(S.n_entries, 0.0), ha(S.n_entries, 0.0), hg((size_t)m.ne * 16);
     std::vector<int32_t> e_cnt(n_edges + 1, 0);
@@ -615,161 +590,13 @@ void build_problem_p2(knp_problem* P) {
                 h_einc[fill[id]++] = (int32_t)(e * npairs + p);
             }
     }
-    // ---- membrane: the P2 nodes of Gamma, facet tables, node -> facet and pair -> facet incidences
-    const int64_t nmv = P->n_mv, nf = P->nf;
-    std::vector<int32_t> h_mvg(2 * nmv);
-    for (int64_t a = 0; a < nmv; ++a) {
-        int32_t x = t2.mnodes[a];
-        h_mvg[a] = t2.loc_i[x];
-        h_mvg[nmv + a] = (int32_t)(Ni + t2.loc_e[x]);
-    }
-    std::vector<int32_t> h_fmv(nf * nfn);
-    std::vector<double> h_farea(nf);
-    for (int64_t f = 0; f < nf; ++f) {
-        for (int s = 0; s < nfn; ++s) {
-            int32_t x = t2.facet_nodes[f * nfn + s];
-            h_fmv[f * nfn + s] = (int32_t)(std::lower_bound(t2.mnodes.begin(), t2.mnodes.end(), x) - t2.mnodes.begin());
-        }
-        h_farea[f] = facet_area(m.coords.data(), dim, &m.facets[f * dim]);
-    }
-    std::vector<int32_t> h_mvf_ptr(nmv + 1, 0);
-    for (int64_t f = 0; f < nf; ++f)
-        for (int s = 0; s < nfn; ++s) h_mvf_ptr[h_fmv[f * nfn + s] + 1]++;
-    for (int64_t a = 0; a < nmv; ++a) h_mvf_ptr[a + 1] += h_mvf_ptr[a];
-    std::vector<int32_t> h_mvf(h_mvf_ptr[nmv]);
-    {
-        std::vector<int32_t> fill(h_mvf_ptr.begin(), h_mvf_ptr.end() - 1);
-        for (int64_t f = 0; f < nf; ++f)
-            for (int s = 0; s < nfn; ++s) h_mvf[fill[h_fmv[f * nfn + s]]++] = (int32_t)((f << 3) | s);
-    }
-    struct PairInc {
-        int64_t key;
-        int32_t packed;
-    };
-    std::vector<PairInc> pinc;
-    pinc.reserve(nf * nfn * nfn);
-    for (int64_t f = 0; f < nf; ++f)
-        for (int sa = 0; sa < nfn; ++sa)
-            for (int sb = 0; sb < nfn; ++sb) {
-                int64_t a = h_fmv[f * nfn + sa], b = h_fmv[f * nfn + sb];
-                pinc.push_back({a * nmv + b, (int32_t)((f << 6) | (sa << 3) | sb)});
-            }
-    std::sort(pinc.begin(), pinc.end(), [](const PairInc& x, const PairInc& y) {
-        return x.key < y.key || (x.key == y.key && x.packed < y.packed);
-    });
-    std::vector<int64_t> pair_key;
-    std::vector<int32_t> h_mp_ptr(1, 0), h_mpf;
-    for (size_t i = 0; i < pinc.size(); ++i) {
-        if (i == 0 || pinc[i].key != pinc[i - 1].key) {
-            pair_key.push_back(pinc[i].key);
-            h_mp_ptr.push_back(h_mp_ptr.back());
-        }
-        h_mpf.push_back(pinc[i].packed);
-        h_mp_ptr.back()++;
-    }
-    const int64_t npairs_m = (int64_t)pair_key.size();
-    P->n_pairs = npairs_m;
-    std::vector<int32_t>& xp = P->h_xptr;
-    std::vector<int32_t>& xc = P->h_xcol;
-    xp.assign(n + 1, 0);
-    for (int64_t q = 0; q < npairs_m; ++q) {
-        int64_t a = pair_key[q] / nmv;
-        xp[h_mvg[a] + 1]++;
-        xp[h_mvg[nmv + a] + 1]++;
-    }
-    for (int64_t r = 0; r < n; ++r) xp[r + 1] += xp[r];
-    xc.assign(xp[n], 0);
-    std::vector<int32_t> h_tgt(4 * npairs_m);
-    {
-        std::vector<int32_t> fill(xp.begin(), xp.end() - 1);
-        for (int64_t q = 0; q < npairs_m; ++q) {
-            int64_t a = pair_key[q] / nmv, b = pair_key[q] % nmv;
-            int32_t gia = h_mvg[a], gea = h_mvg[nmv + a], gib = h_mvg[b], geb = h_mvg[nmv + b];
-            h_tgt[4 * q + 0] = (int32_t)sell_find(S, row_len, gia, gib);
-            h_tgt[4 * q + 1] = (int32_t)sell_find(S, row_len, gea, geb);
-            KNP_REQUIRE(h_tgt[4 * q] >= 0 && h_tgt[4 * q + 1] >= 0, KNP_ERR_INVALID_MESH,
-                        "membrane facet node pair missing from the region pattern");
-            xc[fill[gia]] = geb;
-            h_tgt[4 * q + 2] = fill[gia]++;
-            xc[fill[gea]] = gib;
-            h_tgt[4 * q + 3] = fill[gea]++;
-        }
-    }
-    std::vector<int32_t> xtp(n + 1, 0), xtr(xc.size()), xti(xc.size());
-    for (size_t q = 0; q < xc.size(); ++q) xtp[xc[q] + 1]++;
-    for (int64_t r = 0; r < n; ++r) xtp[r + 1] += xtp[r];
-    {
-        std::vector<int32_t> fill(xtp.begin(), xtp.end() - 1);
-        for (int64_t r = 0; r < n; ++r)
-            for (int32_t q = xp[r]; q < xp[r + 1]; ++q) {
-                int32_t o = fill[xc[q]]++;
-                xtr[o] = (int32_t)r;
-                xti[o] = q;
-            }
-    }
-
-    // ---- uploads
-    p2_upload_tables(st);
-    S.slice_ptr.upload(S.h_slice_ptr, st);
-    S.col.upload(S.h_col, st);
-    P->sell_edge.upload(h_edge, st);
-    P->sell_m.upload(hm, st);
-    P->sell_a.upload(ha, st);
-    P->sell_e.alloc(3 * S.n_entries);
-    P->sell_e.zero(st);
-    P->xptr.upload(xp, st);
-    P->xcol.upload(xc, st);
-    P->xtptr.upload(xtp, st);
-    P->xtrow.upload(xtr, st);
-    P->xtidx.upload(xti, st);
-    P->xe.alloc(std::max<int64_t>(1, 3 * (int64_t)xc.size()));
-    P->xe.zero(st);
-    P->el_nodes.upload(eln, st);
-    P->el_g.upload(hg, st);
-    P->cbar.alloc(3 * m.ne * npairs);
-    P->eptr.upload(e_cnt, st);
-    P->einc.upload(h_einc, st);
-    P->ecoef.upload(h_ecoef, st);
-    P->ak.alloc(std::max<int64_t>(1, 3 * n_edges));
-    P->mv_g.upload(h_mvg, st);
-    P->gates.alloc(3 * nmv);
-    P->gates_new.alloc(3 * nmv);
-    P->mfield.alloc(14 * nmv);
-    P->f_mv.upload(h_fmv, st);
-    P->f_area.upload(h_farea, st);
-    P->f_model.upload(P->facet_model, st);
-    P->f_gleak.upload(P->facet_gleak, st);
-    P->f_mask.upload(P->stim_mask, st);
-    P->mvf_ptr.upload(h_mvf_ptr, st);
-    P->mvf.upload(h_mvf, st);
-    P->mp_ptr.upload(h_mp_ptr, st);
-    P->mpf.upload(h_mpf, st);
-    P->mp_tgt.upload(h_tgt, st);
-    if (!P->source_v[0].empty() || !P->source_v[1].empty()) {
-        // bulk source at the P2 nodes (source arrays are indexed by global P2 node id)
-        std::vector<double> hs(4 * n, 0.0);
-        for (int r = 0; r < 2; ++r) {
-            if (P->source_v[r].empty()) continue;
-            const std::vector<int32_t>& nodes = r == 0 ? t2.nodes_i : t2.nodes_e;
-            const int64_t off = r == 0 ? 0 : Ni;
-            for (size_t j = 0; j < nodes.size(); ++j)
-                for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)nodes[j] * KI + k];
-        }
-        P->src.upload(hs, st);
-    }
-    P->u.alloc(4 * n);
-    P->f.alloc(4 * n);
-    P->f.zero(st);
-    P->sinv.alloc(4 * n);
-    P->svec.alloc(4 * n);
-    P->swt.alloc(4 * n);
-    const knp_problem_desc& d = P->desc;
-    count_launch(nmv ? 2 : 1);
-    k_init_state<<<nblk(n), 256, 0, st>>>(P->u.p, Ni, n, d.c_i0[0], d.c_i0[1], d.c_i0[2], d.c_e0[0], d.c_e0[1],
-                                          d.c_e0[2], d.phi_M0);
-    if (nmv) k_init_gates<<<nblk(nmv), 256, 0, st>>>(P->gates.p, nmv, d.w0[0], d.w0[1], d.w0[2]);
-    KNP_CUDA(cudaGetLastError());
-    KNP_CUDA(cudaStreamSynchronize(st));
+    // ---- membrane: the P2 nodes of Gamma (slots of up to 6 facet nodes: 3 bits)
+    MembraneHost M;
+    build_membrane(P, S, row_len, t2.facet_nodes, nfn, t2.mnodes, t2.loc_i, t2.loc_e, 3, M);
+    P->n_pairs = M.npairs;
+    p2_upload_tables(P->stream);
+    upload_problem(P, h_edge, hm, ha, eln, &hg, 3 * m.ne * npairs, e_cnt, h_einc, h_ecoef, M, t2.nodes_i,
+                   t2.nodes_e);
 }
 
 // Element contributions to the P2 matrices M_r, A_r and A_r^{c} of one region (host only). The
