@@ -59,11 +59,12 @@ def test_p2_assembly_and_operator(name):
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64-amg", "fp32-amg"])
-@pytest.mark.parametrize("name,n_steps", [("2d-leak-16", 5), ("3d-hh-8", 4), ("kir-2d-16", 5)])
-def test_p2_time_steps_match_oracle(name, n_steps, precision):
+@pytest.mark.parametrize("name,n_steps,exact", [("2d-leak-16", 5, "direct"), ("3d-hh-8", 4, "lu_p0"),
+                                                ("kir-2d-16", 5, "direct")])
+def test_p2_time_steps_match_oracle(name, n_steps, exact, precision):
     from paper_2403_04491_gb300 import problem_from_config
     cfg = _cfgs()[name]
-    pb, ref = oracle_run(cfg, n_steps, "direct", degree=2)
+    pb, ref = oracle_run(cfg, n_steps, exact, degree=2)
     _, prob = problem_from_config(cfg, degree=2)
     prob.amg_setup(precision=precision)
     for n in range(1, n_steps + 1):
