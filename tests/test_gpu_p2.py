@@ -81,3 +81,42 @@ def test_p2_adjoint_is_refused():
     _, prob = problem_from_config(make_config(1).with_nx(8), degree=2)
     with pytest.raises(KnpError):
         prob.adjoint_begin()
+
+
+@pytest.mark.slow
+def test_p2_bench_workload_full_size():
+    """The P2 bench workload at its full size (3D HH, 32^3 mesh with P2 elements: the node
+    lattice of the 64^3 P1 workload) in the bench's launch configuration: the operator at 20,000
+    sampled entries, the right-hand side and an operator product against the oracle's assembly;
+    then five steps whose true residuals stay at the solver tolerance and which conserve the
+    charge of the cell and of the extracellular space."""
+    import scipy.sparse as sp
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2).with_nx(32)
+    pb, s0 = oproblem.from_config(cfg, degree=2)
+    A, f, _ = osystem.assemble(pb, s0)
+    _, prob = problem_from_config(cfg, degree=2)
+    assert prob.n_dof == A.shape[0]
+    prob.assemble_step()
+    Acoo = A.tocoo()
+    pick = np.random.default_rng(7).choice(Acoo.nnz, 20000, replace=False)
+    As = sp.coo_matrix((Acoo.data[pick], (Acoo.row[pick], Acoo.col[pick])), shape=A.shape)
+    assert blockscaled_entry_error(pb, As, prob.operator_entries(As.row, As.col)) < 1e-12
+    assert blockwise_vector_error(pb, prob.rhs_get(), f) < 1e-12
+    x = np.random.default_rng(8).standard_normal(A.shape[0])
+    assert blockwise_vector_error(pb, prob.apply_operator(x), A @ x) < 1e-12
+    g, z = pb.geo, pb.z
+
+    def charges(st):
+        qi = sum(z[k] * (g["M_i"] @ st["c_i"][k]) for k in range(3))
+        return np.bincount(pb.topo.node_cell_i, weights=qi), sum(z[k] * (g["M_e"] @ st["c_e"][k]).sum() for k in range(3))
+
+    scale = sum((g["M_e"] @ s0.c_e[k]).sum() for k in range(3))
+    q0 = charges(prob.state_get())
+    prob.amg_setup()
+    for _ in range(5):
+        prob.assemble_step()
+        st = prob.solve(rtol=1e-10)
+        assert st["true_relres"] < 1e-9, st
+    q1 = charges(prob.state_get())
+    assert np.abs(q1[0] - q0[0]).max() < 1e-9 * scale and abs(q1[1] - q0[1]) < 1e-9 * scale
