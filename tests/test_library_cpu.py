@@ -271,3 +271,43 @@ def test_p2_arguments_are_checked(lib):
     with pytest.raises(KnpError) as ei:
         problem_from_config(cfg, mesh=M, degree=3)
     assert ei.value.code == 1 and "degree" in str(ei.value)
+
+
+@pytest.mark.parametrize("dim,nx", [(2, 12), (3, 6)])
+def test_jittered_mesh_topology_and_p2_matrices(lib, dim, nx):
+    """An unstructured-looking mesh: the structured mesh with its interior vertices moved at
+    random by up to a fifth of the spacing (no element inverts). The library's P1 and P2 tables,
+    the pin and the P2 region matrices equal the oracle's."""
+    from oracle import p2
+    from oracle.topology import build_topology
+    from paper_2403_04491_gb300 import Mesh
+    L = 1e-6
+    coords, elems = structured_mesh(dim, nx, L)
+    rng = np.random.default_rng(11 + dim)
+    interior = np.all((coords > 1e-12 * L) & (coords < L * (1 - 1e-12)), axis=1)
+    coords = coords.copy()
+    coords[interior] += rng.uniform(-0.2, 0.2, (interior.sum(), dim)) * (L / nx)
+    cen = coords[elems].mean(axis=1) / L
+    tag = np.all((cen > 0.3) & (cen < 0.7), axis=1).astype(np.int32)
+    M = Mesh(coords, elems, tag, pin_point=np.full(dim, 0.5 * L))
+    T = build_topology(coords, elems, tag, pin_point=np.full(dim, 0.5 * L))
+    ni, ne = M.nodes()
+    assert np.array_equal(ni, T.nodes_i) and np.array_equal(ne, T.nodes_e)
+    assert M.info["pin_vertex"] == T.pin_vertex
+    T2 = p2.build_topology(coords, elems, tag, pin_point=np.full(dim, 0.5 * L))
+    P = M.p2()
+    for k, ref in (("elem_nodes", T2.elem_nodes), ("facet_nodes", T2.facet_nodes), ("nodes_e", T2.nodes_e),
+                   ("membrane_nodes", T2.membrane_nodes)):
+        assert np.array_equal(P[k], ref), k
+    assert P["pin_node"] == T2.pin_node
+    from oracle import system
+    pb = system.Problem(topo=T2, coords=coords, elems=elems, R=1, T=1, F=1, Cm=1, z=np.ones(3), D_i=np.ones(3),
+                        D_e=np.ones(3), dt=1.0, facet_model=np.zeros(len(T2.facets), np.int32),
+                        facet_gleak=np.zeros((len(T2.facets), 3)), fe=p2)
+    p2.discretize(pb)
+    c = rng.uniform(1, 2, T2.N_i)
+    Mi, Ai, Aci = M.p2_region_matrices(0, c)
+    Ac_ref = p2.weighted_stiffness(pb.geo["cache_i"], c, pb.geo["en_i"], T2.N_i)
+    for a, b in ((Mi, pb.geo["M_i"]), (Ai, pb.geo["A_i"]), (Aci, Ac_ref)):
+        d = (a - b).tocoo()
+        assert (abs(d.data).max() if d.nnz else 0.0) <= 1e-12 * abs(b).max()
