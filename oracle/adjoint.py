@@ -38,6 +38,8 @@ class TorchForm:
     """Static pieces of the discretisation as torch tensors."""
 
     def __init__(self, pb: system.Problem):
+        if pb.fe is not fem:
+            raise ValueError("the adjoint residual form covers P1 elements only")
         g = pb.geo
         t = pb.topo
         self.pb = pb

@@ -447,3 +447,10 @@ def test_p2_third_order_in_space():
     op = [np.log2(ep[k] / ep[k + 1]) for k in range(2)]
     assert all(2.8 <= o <= 3.7 for o in oc), oc
     assert all(2.8 <= o <= 3.7 for o in op), op
+
+
+def test_oracle_adjoint_refuses_p2():
+    from oracle import adjoint
+    pb, _ = problem.from_config(make_config(1).with_nx(8), degree=2)
+    with pytest.raises(ValueError):
+        adjoint.TorchForm(pb)
