@@ -10,7 +10,7 @@ namespace knp {
 // element: the moments mu_q = sum_j mom[q][j] c_j against 1, lambda_x, lambda_x lambda_y, then
 // sum_t coef_t G[a_t][b_t] mu[q_t] with G = |T| grad lambda_a . grad lambda_b (row-major 4x4).
 template <int D>
-__host__ __device__ inline void p2_pair_values(const P2Dev& T, const double* __restrict__ G,
+__host__ __device__ __forceinline__ void p2_pair_values(const P2Dev& T, const double* __restrict__ G,
                                                const double* __restrict__ c, double* __restrict__ out) {
     constexpr int NPE = (D + 1) * (D + 2) / 2;
     constexpr int NMOM = 1 + (D + 1) + (D + 1) * (D + 2) / 2;
