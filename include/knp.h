@@ -192,7 +192,12 @@ typedef struct {
 
 /* Creates device state for one simulation on `stream`; u_0 as in Section 2.3
  * with phi_i^0 = phi_M0 and phi_e^0 = 0, gates w_0 at every membrane vertex.
- * Errors: KNP_ERR_INVALID_ARG, KNP_ERR_OOM, KNP_ERR_CUDA. */
+ * Errors: KNP_ERR_INVALID_ARG, KNP_ERR_OOM, KNP_ERR_CUDA.
+ * Dry run: with the environment variable KNP_DRY_RUN_TABLES=<file>, the call builds the
+ * problem's host tables (pattern, static values, incidences, membrane tables, source), appends
+ * each of them to <file> as (int64 name length, int64 count, int64 element size, name, data),
+ * does no device work at all and returns KNP_ERR_STATE with no handle. It lets a problem set-up
+ * be inspected on a machine without a GPU. */
 knp_status knp_problem_create(const knp_mesh* mesh, const knp_problem_desc* desc, void* stream,
                               knp_problem** out);
 void knp_problem_destroy(knp_problem* prob);

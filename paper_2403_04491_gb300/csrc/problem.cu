@@ -5,6 +5,8 @@
 // M_{r,Gamma}, M_{rq,Gamma}; Section 2.3 initial state.)
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -325,8 +327,44 @@ void build_membrane(knp_problem* P, const SellPattern& S, const std::vector<int3
     }
 }
 
-// Uploads of the operator, assembly and membrane tables, the bulk source at the region nodes
-// (source_v indexed by the ids in nodes_i / nodes_e), the state vectors and u_0, w_0.
+// The bulk source at the region nodes (source_v indexed by the ids in nodes_i / nodes_e), empty
+// without a source.
+std::vector<double> node_source(const knp_problem* P, const std::vector<int32_t>& nodes_i,
+                                const std::vector<int32_t>& nodes_e) {
+    std::vector<double> hs;
+    if (P->source_v[0].empty() && P->source_v[1].empty()) return hs;
+    hs.assign(4 * P->n_nodes, 0.0);
+    for (int r = 0; r < 2; ++r) {
+        if (P->source_v[r].empty()) continue;
+        const std::vector<int32_t>& ids = r == 0 ? nodes_i : nodes_e;
+        const int64_t off = r == 0 ? 0 : P->N_i;
+        for (size_t j = 0; j < ids.size(); ++j)
+            for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)ids[j] * KI + k];
+    }
+    return hs;
+}
+
+// KNP_DRY_RUN_TABLES=<file>: write the host tables instead of uploading them (see knp.h).
+class TableWriter {
+  public:
+    explicit TableWriter(const char* path) : f_(std::fopen(path, "ab")) {
+        KNP_REQUIRE(f_, KNP_ERR_INVALID_ARG, "cannot open %s", path);
+    }
+    ~TableWriter() { std::fclose(f_); }
+    template <class T>
+    void put(const char* name, const std::vector<T>& v) {
+        const int64_t head[3] = {(int64_t)std::strlen(name), (int64_t)v.size(), (int64_t)sizeof(T)};
+        std::fwrite(head, sizeof(head), 1, f_);
+        std::fwrite(name, 1, std::strlen(name), f_);
+        if (!v.empty()) std::fwrite(v.data(), sizeof(T), v.size(), f_);
+    }
+
+  private:
+    std::FILE* f_;
+};
+
+// Uploads of the operator, assembly and membrane tables, the bulk source, the state vectors and
+// u_0, w_0 (and, for P2, the reference tables in constant memory).
 void upload_problem(knp_problem* P, const std::vector<int32_t>& h_edge, const std::vector<double>& hm,
                     const std::vector<double>& ha, const std::vector<int32_t>& eln, const std::vector<double>* hg,
                     int64_t cbar_len, const std::vector<int32_t>& e_cnt, const std::vector<int32_t>& h_einc,
@@ -335,6 +373,39 @@ void upload_problem(knp_problem* P, const std::vector<int32_t>& h_edge, const st
     cudaStream_t st = P->stream;
     SellPattern& S = P->sell;
     const int64_t n = P->n_nodes, Ni = P->N_i, nmv = P->n_mv;
+    const std::vector<double> hs = node_source(P, nodes_i, nodes_e);
+    if (const char* path = std::getenv("KNP_DRY_RUN_TABLES")) {
+        {
+            TableWriter w(path);
+            w.put("info", std::vector<int64_t>{P->degree, P->dim, P->N_i, P->N_e, P->pin, P->n_mv, P->n_elem});
+            w.put("slice_ptr", S.h_slice_ptr);
+            w.put("col", S.h_col);
+            w.put("sell_edge", h_edge);
+            w.put("sell_m", hm);
+            w.put("sell_a", ha);
+            w.put("xptr", P->h_xptr);
+            w.put("xcol", P->h_xcol);
+            w.put("el_nodes", eln);
+            if (hg) w.put("el_g", *hg);
+            w.put("eptr", e_cnt);
+            w.put("einc", h_einc);
+            w.put("ecoef", h_ecoef);
+            w.put("mv_g", M.mvg);
+            w.put("f_mv", M.fmv);
+            w.put("f_area", M.farea);
+            w.put("f_model", P->facet_model);
+            w.put("f_gleak", P->facet_gleak);
+            w.put("f_mask", P->stim_mask);
+            w.put("mvf_ptr", M.mvf_ptr);
+            w.put("mvf", M.mvf);
+            w.put("mp_ptr", M.mp_ptr);
+            w.put("mpf", M.mpf);
+            w.put("mp_tgt", M.tgt);
+            w.put("src", hs);
+        }
+        KNP_FAIL(KNP_ERR_STATE, "dry run: the problem's host tables were written to %s; no device work", path);
+    }
+    if (P->degree == 2) p2_upload_tables(st);
     S.slice_ptr.upload(S.h_slice_ptr, st);
     S.col.upload(S.h_col, st);
     P->sell_edge.upload(h_edge, st);
@@ -370,18 +441,7 @@ void upload_problem(knp_problem* P, const std::vector<int32_t>& h_edge, const st
     P->mp_ptr.upload(M.mp_ptr, st);
     P->mpf.upload(M.mpf, st);
     P->mp_tgt.upload(M.tgt, st);
-    if (!P->source_v[0].empty() || !P->source_v[1].empty()) {
-        // bulk source at the nodes: the intracellular values for i-nodes, the extracellular ones for e-nodes
-        std::vector<double> hs(4 * n, 0.0);
-        for (int r = 0; r < 2; ++r) {
-            if (P->source_v[r].empty()) continue;
-            const std::vector<int32_t>& ids = r == 0 ? nodes_i : nodes_e;
-            const int64_t off = r == 0 ? 0 : Ni;
-            for (size_t j = 0; j < ids.size(); ++j)
-                for (int k = 0; k < KI; ++k) hs[4 * (off + j) + k] = P->source_v[r][(size_t)ids[j] * KI + k];
-        }
-        P->src.upload(hs, st);
-    }
+    if (!hs.empty()) P->src.upload(hs, st);
     P->u.alloc(4 * n);
     P->f.alloc(4 * n);
     P->f.zero(st);
@@ -594,7 +654,6 @@ void build_problem_p2(knp_problem* P) {
     MembraneHost M;
     build_membrane(P, S, row_len, t2.facet_nodes, nfn, t2.mnodes, t2.loc_i, t2.loc_e, 3, M);
     P->n_pairs = M.npairs;
-    p2_upload_tables(P->stream);
     upload_problem(P, h_edge, hm, ha, eln, &hg, 3 * m.ne * npairs, e_cnt, h_einc, h_ecoef, M, t2.nodes_i,
                    t2.nodes_e);
 }
