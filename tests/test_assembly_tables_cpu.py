@@ -9,8 +9,8 @@ following the kernels' loops, from the oracle's membrane update; the operator pr
 right-hand side must equal the oracle's assembly of Eq. 4.3.
 
 For P1 the kernels themselves are checked against the oracle on the GPU, so the P1 cases check
-this replay. The P2 cases then check the P2 tables and the P2 kernels' arithmetic, which have
-not run on a GPU yet (Section 3.3 with p = 2)."""
+this replay. The P2 cases then check the P2 tables and the P2 kernels' arithmetic on the CPU
+(Section 3.3 with p = 2), beside their GPU parity tests."""
 import os
 
 import numpy as np

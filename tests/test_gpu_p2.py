@@ -1,12 +1,11 @@
 """GPU parity of the P2 path (Section 3.3 with p = 2) through the C ABI against the P2 oracle.
 
-The P2 kernels (element pair values of A_r^{k}, P2 membrane pairs and right-hand side) have not
-run on a GPU yet, so these tests run only when KNP_P2_GPU=1 is set. Their host side is checked
-on the CPU: the P2 node tables, the static M_r and A_r, and the per-step element arithmetic of
-A_r^{k} (tests/test_library_cpu.py). Same bars as the P1 parity tests.
+The P2 kernels (element pair values of A_r^{k}, P2 membrane pairs and right-hand side) are
+compared with the P2 oracle's assembly entry by entry, and whole time steps with its states.
+Their host side is also checked on the CPU: the P2 node tables, the static M_r and A_r, and the
+per-step element arithmetic of A_r^{k} (tests/test_library_cpu.py). Same bars as the P1 parity
+tests.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -15,9 +14,7 @@ from oracle import problem as oproblem, system as osystem
 from synth import make_config
 from synth.configs import model_a
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("KNP_P2_GPU") != "1",
-                                 reason="the P2 kernels have not run on a GPU yet (set KNP_P2_GPU=1)")]
+pytestmark = pytest.mark.gpu
 
 TOL = 1e-8
 
