@@ -223,7 +223,10 @@ typedef struct {
     double cheb_ratio;          /* lower eigenvalue bound = lambda_max / cheb_ratio (4) */
     double theta_coarse;        /* strength threshold on levels >= 1 (< 0: same as theta; 0) */
     double p_drop;              /* drop prolongator entries below p_drop x the row's largest (0: keep all) */
-    int32_t host_setup;         /* 1: build the hierarchy on the host (reference path); 0: on the GPU */
+    int32_t host_setup;         /* 1: build the hierarchy on the host (the reference a test compares the
+                                   GPU build with); 0: on the GPU, with no host fallback (rows of P or of
+                                   the Galerkin products too long for the short-row kernels are finished
+                                   by the GPU's long-row kernels) */
     int32_t inner_cg_max_it;    /* 0: P_0^{-1} is one V-cycle (AMG(P_0), Section 4.2). > 0: CG(P_0) of
                                    Section 6.3: each of the 2(|K|+1) field blocks of P_0 is solved by
                                    CG preconditioned with the V-cycle, to inner_cg_rtol or this many
@@ -233,9 +236,23 @@ typedef struct {
 
 /* Smoothed-aggregation AMG on P_0 (Eq. 4.4) assembled from the initial
  * state and reused for every step (Section 4.2). Must follow
- * knp_problem_create and precede knp_solve. Errors: KNP_ERR_INVALID_ARG,
- * KNP_ERR_OOM, KNP_ERR_NUMERIC (singular coarse matrix), KNP_ERR_CUDA. */
+ * knp_problem_create and precede knp_solve. P_0 is taken from the assembled
+ * operator on the GPU; with host_setup = 0 the hierarchy is built there too and
+ * handed to the V-cycle without passing through host memory. Synchronises the
+ * problem's stream. Errors: KNP_ERR_INVALID_ARG, KNP_ERR_OOM, KNP_ERR_NUMERIC
+ * (a non-positive diagonal of P_0, a singular coarse matrix), KNP_ERR_CUDA. */
 knp_status knp_amg_setup(knp_problem* prob, const knp_amg_opts* opts);
+
+/* How the last knp_amg_setup built the hierarchy (Section 4.2's setup, which the paper
+ * counts as initialisation). */
+typedef struct {
+    int32_t on_gpu;           /* 1: built on the GPU; 0: on the host (host_setup = 1) */
+    int64_t long_rows_p;      /* rows of the smoothed prolongators finished by the long-row kernel */
+    int64_t long_rows_rap;    /* rows of A P and R (A P) finished by the long-row kernel */
+    double setup_ms;          /* wall time of knp_amg_setup, P_0 extraction included */
+} knp_amg_setup_record;
+/* Errors: KNP_ERR_INVALID_ARG, KNP_ERR_STATE (no hierarchy yet). */
+knp_status knp_amg_setup_info(const knp_problem* prob, knp_amg_setup_record* rec);
 
 typedef struct {
     double rtol;       /* on the preconditioned residual: ||S M^-1 r||_g <= rtol max(||S x_c||_g,
@@ -351,9 +368,11 @@ knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* 
  * nothing: its work vectors live in one static device array of 32 MiB that every GPU which
  * loads the library holds until the process exits. Hierarchies whose work vectors need more
  * than that (about 120,000 nodes with the FP64 hierarchy, 180,000 with FP32) are rejected with
- * KNP_ERR_INVALID_ARG and a message giving the size. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. All calls share the array and keep the last call's
+ * KNP_ERR_INVALID_ARG and a message giving the size. The device that is current at the call
+ * must be the one the problem was created on (else KNP_ERR_INVALID_ARG), because the array is
+ * looked up on the current device. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. All calls share the array and keep the last call's
  * contents, so calls that overlap on the GPU (other streams, other problems, other host
  * threads) race and must be serialised by the caller. Stream-ordered on the problem's
  * stream; returns without synchronising. Errors: KNP_ERR_INVALID_ARG, KNP_ERR_STATE (no

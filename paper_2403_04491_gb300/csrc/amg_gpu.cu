@@ -16,8 +16,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "amg.h"
-#include "problem.h"
+#include "amg_gpu.h"
 
 namespace knp {
 
@@ -86,12 +85,6 @@ int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t 
 }
 
 // ------------------------------------------------------------------ level basics
-struct DCsr4 {
-    int64_t n_rows = 0, n_cols = 0, nnz = 0;
-    DArray<int64_t> ptr;
-    DArray<int32_t> col;
-    DArray<double> val;
-};
 
 // diagonal, D^-1 (with an empty field row given a unit diagonal, as on the host), |s_ii|
 __global__ void k_diag(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
@@ -289,16 +282,18 @@ __global__ void k_singletons(int64_t n, int64_t base, const int64_t* __restrict_
 }
 
 // ------------------------------------------------------------------ smoothed prolongator
-constexpr int PMAX = 96;    // distinct aggregates in one row of P (rows beyond: host fallback)
+constexpr int PMAX = 96;    // distinct aggregates in one row of P (longer rows: k_prolong_long)
 
 // Row i of P: slots in order of first appearance (agg(i), then the aggregates of row i of A),
 // accumulated in that order as on the host, then sorted by column; pass 0 counts, pass 1 writes.
+// A row with more than PMAX distinct aggregates is left to k_prolong_long: pass 0 appends it to
+// long_rows[*n_long] (pass 1 skips it).
 __global__ void k_prolong(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                           const double* __restrict__ val, const double* __restrict__ dinv,
                           const double* __restrict__ B, const int32_t* __restrict__ agg, double om0, double om1,
                           double om2, double om3, double p_drop, int pass, int64_t* __restrict__ cnt,
                           const int64_t* __restrict__ pptr, int32_t* __restrict__ pcol, double* __restrict__ pval,
-                          int* __restrict__ overflow) {
+                          int64_t* __restrict__ long_rows, unsigned long long* __restrict__ n_long, int pmax) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double om[4] = {om0, om1, om2, om3};
@@ -308,7 +303,7 @@ __global__ void k_prolong(int64_t n, const int64_t* __restrict__ ptr, const int3
     auto slot = [&](int32_t c) -> int {
         for (int q = 0; q < m; ++q)
             if (keys[q] == c) return q;
-        if (m >= PMAX) return -1;
+        if (m >= pmax) return -1;
         keys[m] = c;
         for (int f = 0; f < 4; ++f) acc[m][f] = 0.0;
         return m++;
@@ -319,7 +314,10 @@ __global__ void k_prolong(int64_t n, const int64_t* __restrict__ ptr, const int3
         int64_t j = col[t];
         int q = slot(agg[j]);
         if (q < 0) {
-            atomicExch(overflow, 1);
+            if (!pass) {
+                cnt[i] = 0;
+                long_rows[atomicAdd(n_long, 1ULL)] = i;
+            }
             return;
         }
         for (int f = 0; f < 4; ++f) acc[q][f] -= om[f] * dinv[4 * i + f] * val[4 * t + f] * B[4 * j + f];
@@ -352,6 +350,176 @@ __global__ void k_prolong(int64_t n, const int64_t* __restrict__ ptr, const int3
     }
     if (!pass) cnt[i] = c;
 }
+
+// ------------------------------------------------------------------ long rows
+// Rows with more distinct columns than the register slots of k_prolong or the shared-memory hash
+// of the SpGEMM hold are finished by one block per row with a dense accumulator over the n_cols
+// output columns in global memory: acc [n_cols][4] and mark [n_cols], one such workspace per
+// block, zero between rows. The terms reach each output slot in the same order as in the
+// short-row kernels and on the host (one thread adds a P row's terms one after another; the
+// SpGEMM adds the entries of one row of B at a time, whose columns are distinct), so the values
+// are the same. Reading the marks in column order gives the row sorted.
+
+// Ordered compaction of the marked columns of [0, n_cols): emit(c, rank) for every c with
+// mark[c] != 0, rank = the number of marked columns before c. Returns the count. Called by all
+// threads of the block (blockDim.x a multiple of 32, at most 1024).
+template <class Emit>
+__device__ int64_t block_marked_scan(int64_t n_cols, const int32_t* __restrict__ mark, Emit emit) {
+    __shared__ int wcnt[32];
+    __shared__ int64_t base_s, chunk_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < n_cols; c0 += blockDim.x) {
+        const int64_t c = c0 + tid;
+        const bool m = c < n_cols && mark[c] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, m);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        if (tid == 0) {
+            int s = 0;
+            for (int w = 0; w < nw; ++w) {
+                const int t = wcnt[w];
+                wcnt[w] = s;
+                s += t;
+            }
+            chunk_s = s;
+        }
+        __syncthreads();
+        if (m) emit(c, base_s + wcnt[wid] + __popc(bal & ((1u << lane) - 1u)));
+        __syncthreads();
+        if (tid == 0) base_s += chunk_s;
+        __syncthreads();
+    }
+    return base_s;
+}
+
+// Long rows of P (see k_prolong): pass 0 writes cnt[i], pass 1 the row at pptr[i].
+__global__ void __launch_bounds__(256) k_prolong_long(int64_t n_long, const int64_t* __restrict__ rows, int64_t na,
+                                                      const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                      const double* __restrict__ val, const double* __restrict__ dinv,
+                                                      const double* __restrict__ B, const int32_t* __restrict__ agg,
+                                                      double om0, double om1, double om2, double om3, double p_drop,
+                                                      int pass, int64_t* __restrict__ cnt,
+                                                      const int64_t* __restrict__ pptr, int32_t* __restrict__ pcol,
+                                                      double* __restrict__ pval, double* __restrict__ ws_acc,
+                                                      int32_t* __restrict__ ws_mark) {
+    double* acc = ws_acc + (int64_t)blockIdx.x * na * 4;
+    int32_t* mark = ws_mark + (int64_t)blockIdx.x * na;
+    __shared__ double rmax[4];
+    const double om[4] = {om0, om1, om2, om3};
+    for (int64_t q = blockIdx.x; q < n_long; q += gridDim.x) {
+        const int64_t i = rows[q];
+        const int64_t a0 = ptr[i], a1 = ptr[i + 1];
+        const int64_t ai = agg[i];
+        if (threadIdx.x == 0) mark[ai] = 1;
+        for (int64_t t = a0 + threadIdx.x; t < a1; t += blockDim.x) mark[agg[col[t]]] = 1;
+        if (threadIdx.x == 0) {
+            for (int f = 0; f < 4; ++f) acc[4 * ai + f] += B[4 * i + f];
+            for (int64_t t = a0; t < a1; ++t) {
+                const int64_t j = col[t], aj = agg[j];
+                for (int f = 0; f < 4; ++f) acc[4 * aj + f] -= om[f] * dinv[4 * i + f] * val[4 * t + f] * B[4 * j + f];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            const int f = threadIdx.x;
+            double r = fabs(acc[4 * ai + f]);
+            for (int64_t t = a0; t < a1; ++t) r = fmax(r, fabs(acc[4 * (int64_t)agg[col[t]] + f]));
+            rmax[f] = r;
+        }
+        __syncthreads();
+        if (p_drop > 0) {
+            for (int64_t t = a0 + threadIdx.x; t < a1; t += blockDim.x) {
+                const int64_t c = agg[col[t]];
+                bool keep = c == ai;
+                for (int f = 0; f < 4 && !keep; ++f) keep = fabs(acc[4 * c + f]) >= p_drop * rmax[f];
+                if (!keep) mark[c] = 0;
+            }
+            __syncthreads();
+        }
+        const int64_t w = pass ? pptr[i] : 0;
+        const int64_t m = block_marked_scan(na, mark, [&](int64_t c, int64_t r) {
+            if (pass) {
+                pcol[w + r] = (int32_t)c;
+                for (int f = 0; f < 4; ++f) pval[4 * (w + r) + f] = acc[4 * c + f];
+            }
+        });
+        if (!pass && threadIdx.x == 0) cnt[i] = m;
+        // clear the workspace for the next row
+        if (threadIdx.x == 0) {
+            mark[ai] = 0;
+            for (int f = 0; f < 4; ++f) acc[4 * ai + f] = 0.0;
+        }
+        for (int64_t t = a0 + threadIdx.x; t < a1; t += blockDim.x) {
+            const int64_t c = agg[col[t]];
+            mark[c] = 0;
+            for (int f = 0; f < 4; ++f) acc[4 * c + f] = 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// Long rows of C = A B (see row_keys): pass 0 writes cnt[row], pass 1 the sorted row at cptr[row].
+__global__ void __launch_bounds__(256) k_spgemm_long(int64_t n_long, const int64_t* __restrict__ rows, int64_t n_cols,
+                                                     const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
+                                                     const double* __restrict__ aval, const int64_t* __restrict__ bptr,
+                                                     const int32_t* __restrict__ bcol, const double* __restrict__ bval,
+                                                     int pass, int64_t* __restrict__ cnt,
+                                                     const int64_t* __restrict__ cptr, int32_t* __restrict__ ccol,
+                                                     double* __restrict__ cval, double* __restrict__ ws_acc,
+                                                     int32_t* __restrict__ ws_mark) {
+    double* acc = ws_acc + (int64_t)blockIdx.x * n_cols * 4;
+    int32_t* mark = ws_mark + (int64_t)blockIdx.x * n_cols;
+    for (int64_t q = blockIdx.x; q < n_long; q += gridDim.x) {
+        const int64_t row = rows[q];
+        for (int64_t t = aptr[row]; t < aptr[row + 1]; ++t) {
+            const int64_t k = acol[t];
+            const double a[4] = {aval[4 * t], aval[4 * t + 1], aval[4 * t + 2], aval[4 * t + 3]};
+            for (int64_t u = bptr[k] + threadIdx.x; u < bptr[k + 1]; u += blockDim.x) {
+                const int64_t c = bcol[u];
+                mark[c] = 1;
+                if (pass)
+                    for (int f = 0; f < 4; ++f) acc[4 * c + f] += a[f] * bval[4 * u + f];
+            }
+            if (pass) __syncthreads();   // the next row of B may hit the same columns
+        }
+        __syncthreads();
+        const int64_t w = pass ? cptr[row] : 0;
+        const int64_t m = block_marked_scan(n_cols, mark, [&](int64_t c, int64_t r) {
+            if (pass) {
+                ccol[w + r] = (int32_t)c;
+                for (int f = 0; f < 4; ++f) cval[4 * (w + r) + f] = acc[4 * c + f];
+            }
+        });
+        if (!pass && threadIdx.x == 0) cnt[row] = m;
+        for (int64_t t = aptr[row]; t < aptr[row + 1]; ++t) {
+            const int64_t k = acol[t];
+            for (int64_t u = bptr[k] + threadIdx.x; u < bptr[k + 1]; u += blockDim.x) {
+                const int64_t c = bcol[u];
+                mark[c] = 0;
+                for (int f = 0; f < 4; ++f) acc[4 * c + f] = 0.0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Workspace for the long-row kernels: as many blocks as rows, within `budget` bytes.
+struct LongRowWork {
+    DArray<double> acc;
+    DArray<int32_t> mark;
+    unsigned blocks = 0;
+    void setup(int64_t n_long, int64_t n_cols, cudaStream_t st, size_t budget = size_t(1) << 30) {
+        const size_t per = (size_t)std::max<int64_t>(n_cols, 1) * (4 * sizeof(double) + sizeof(int32_t));
+        const int64_t fit = (int64_t)std::max<size_t>(1, budget / per);
+        blocks = (unsigned)std::min<int64_t>({n_long, fit, 4096});
+        acc.alloc((size_t)blocks * std::max<int64_t>(n_cols, 1) * 4);
+        mark.alloc((size_t)blocks * std::max<int64_t>(n_cols, 1));
+        acc.zero(st);
+        mark.zero(st);
+    }
+};
 
 __global__ void k_coarse_B(int64_t n, const int32_t* __restrict__ agg, const double* __restrict__ B,
                            unsigned long long* __restrict__ Bc_bits) {
@@ -487,20 +655,21 @@ __device__ void warp_bitonic_sort(int32_t* a, int m, int lane) {
         }
 }
 
-// keys of row `row` of C into sorted[0..count); returns count (or -1 on overflow)
+// keys of row `row` of C into sorted[0..count); returns count, or -1 when the row has kcap keys or
+// more (kcap <= hcap / 2 keeps the table at most half full)
 __device__ int row_keys(int64_t row, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
                         const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol, int32_t* table,
-                        int32_t* sorted, int hcap, int* count, int lane) {
+                        int32_t* sorted, int hcap, int kcap, int* count, int lane) {
     for (int h = lane; h < hcap; h += 32) table[h] = -1;
     if (lane == 0) *count = 0;
     __syncwarp();
     for (int64_t t = aptr[row]; t < aptr[row + 1]; ++t) {
         int64_t k = acol[t];
         for (int64_t u = bptr[k] + lane; u < bptr[k + 1]; u += 32) {
-            if (*count < hcap / 2) hash_insert(table, hcap, bcol[u], count);
+            if (*count < kcap) hash_insert(table, hcap, bcol[u], count);
         }
         __syncwarp();
-        if (*count >= hcap / 2) return -1;
+        if (*count >= kcap) return -1;
     }
     __syncwarp();
     int m = *count;
@@ -523,7 +692,8 @@ __device__ int row_keys(int64_t row, const int64_t* __restrict__ aptr, const int
 
 __global__ void k_spgemm_count(int64_t n, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
                                const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol, int hcap,
-                               int64_t* __restrict__ cnt, int* __restrict__ overflow) {
+                               int kcap, int64_t* __restrict__ cnt, int64_t* __restrict__ long_rows,
+                               unsigned long long* __restrict__ n_long) {
     extern __shared__ int32_t smem[];
     const int wib = threadIdx.x / 32, lane = threadIdx.x % 32, wpb = blockDim.x / 32;
     int32_t* table = smem + (int64_t)wib * (2 * hcap + 1);
@@ -531,9 +701,9 @@ __global__ void k_spgemm_count(int64_t n, const int64_t* __restrict__ aptr, cons
     int* count = sorted + hcap;
     int64_t row = (int64_t)blockIdx.x * wpb + wib;
     if (row >= n) return;
-    int m = row_keys(row, aptr, acol, bptr, bcol, table, sorted, hcap, count, lane);
+    int m = row_keys(row, aptr, acol, bptr, bcol, table, sorted, hcap, kcap, count, lane);
     if (lane == 0) {
-        if (m < 0) atomicExch(overflow, 1);
+        if (m < 0) long_rows[atomicAdd(n_long, 1ULL)] = row;   // finished by k_spgemm_long
         cnt[row] = m < 0 ? 0 : m;
     }
 }
@@ -541,7 +711,7 @@ __global__ void k_spgemm_count(int64_t n, const int64_t* __restrict__ aptr, cons
 __global__ void k_spgemm_fill(int64_t n, const int64_t* __restrict__ aptr, const int32_t* __restrict__ acol,
                               const double* __restrict__ aval, const int64_t* __restrict__ bptr,
                               const int32_t* __restrict__ bcol, const double* __restrict__ bval, int hcap,
-                              const int64_t* __restrict__ cptr, int32_t* __restrict__ ccol,
+                              int kcap, const int64_t* __restrict__ cptr, int32_t* __restrict__ ccol,
                               double* __restrict__ cval) {
     extern __shared__ int32_t smem[];
     const int wib = threadIdx.x / 32, lane = threadIdx.x % 32, wpb = blockDim.x / 32;
@@ -550,7 +720,7 @@ __global__ void k_spgemm_fill(int64_t n, const int64_t* __restrict__ aptr, const
     int* count = sorted + hcap;
     int64_t row = (int64_t)blockIdx.x * wpb + wib;
     if (row >= n) return;
-    int m = row_keys(row, aptr, acol, bptr, bcol, table, sorted, hcap, count, lane);
+    int m = row_keys(row, aptr, acol, bptr, bcol, table, sorted, hcap, kcap, count, lane);
     if (m < 0) return;
     const int64_t base = cptr[row];
     double* out = cval + 4 * base;
@@ -587,26 +757,93 @@ __global__ void k_row_bound(int64_t n, const int64_t* __restrict__ aptr, const i
     atomicMax(maxb, b);
 }
 
-void download(const DCsr4& d, HostCsr4& h, cudaStream_t st) {
-    h.n_rows = d.n_rows;
-    h.n_cols = d.n_cols;
-    d.ptr.download(h.ptr, st);
-    d.col.download(h.col, st);
-    d.val.download(h.val, st);
-    KNP_CUDA(cudaStreamSynchronize(st));
+// B = 1 per field except the pinned row's potential field (the near-null vectors of P_0)
+__global__ void k_near_null(int64_t n4, int64_t pin4, double* __restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n4) b[i] = i == pin4 ? 0.0 : 1.0;
 }
 
-void upload(const HostCsr4& h, DCsr4& d, cudaStream_t st) {
-    d.n_rows = h.n_rows;
-    d.n_cols = h.n_cols;
-    d.nnz = h.nnz();
-    d.ptr.upload(h.ptr, st);
-    d.col.upload(h.col, st);
-    d.val.upload(h.val, st);
+// the potential field of every entry (the strength scalar of the coarser levels)
+__global__ void k_field3(int64_t nnz, const double* __restrict__ val, double* __restrict__ out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < nnz) out[t] = val[4 * t + 3];
 }
 
-// C = A B on the device; false if a row overflowed the shared-memory hash (caller falls back)
-bool spgemm_gpu(const DCsr4& A, const DCsr4& B, DCsr4& C, cudaStream_t st) {
+// ------------------------------------------------------------------ P_0 from A_0 (Eq. 4.4)
+// Row r of the region pattern: the sliced-ELL row up to its padding, which repeats the row id
+// after the sorted columns.
+__device__ __forceinline__ int64_t sell_row_len(int64_t r, const int64_t* __restrict__ slice_ptr,
+                                                const int32_t* __restrict__ scol) {
+    const int64_t s = r / SELL_C, base = slice_ptr[s] + r % SELL_C;
+    const int64_t w = (slice_ptr[s + 1] - slice_ptr[s]) / SELL_C;
+    int32_t prev = -1;
+    int64_t k = 0;
+    for (; k < w; ++k) {
+        const int32_t c = scol[base + k * SELL_C];
+        if (c <= prev) break;
+        prev = c;
+    }
+    return k;
+}
+
+__global__ void k_p0_count(int64_t n, const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ scol,
+                           int64_t* __restrict__ cnt) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n) cnt[r] = sell_row_len(r, slice_ptr, scol);
+}
+
+// Field values of P_0 per entry: c^k rows M + tau_r^k A; the potential row sum_k z_k e^k (which is
+// sum_k z_k tau~_r^k A_r^{k,0} + C_m/F M_Gamma on the pattern); the pinned row and column of phi_e
+// become the identity. Also the strength scalar (a) and the diagonal of every field.
+__global__ void k_p0_fill(int64_t n, int64_t N_i, const int64_t* __restrict__ slice_ptr,
+                          const int32_t* __restrict__ scol, const double* __restrict__ m, const double* __restrict__ a,
+                          const double* __restrict__ e, int64_t ne, RegionCoef ri, RegionCoef re, double z0,
+                          double z1, double z2, int64_t pin, const int64_t* __restrict__ ptr, int32_t* __restrict__ col,
+                          double* __restrict__ val, double* __restrict__ strength, double* __restrict__ diag) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const RegionCoef& rc = r < N_i ? ri : re;
+    const double z[3] = {z0, z1, z2};
+    const int64_t s = r / SELL_C, base = slice_ptr[s] + r % SELL_C;
+    const int64_t len = ptr[r + 1] - ptr[r];
+    for (int f = 0; f < 4; ++f) diag[4 * r + f] = 0.0;
+    for (int64_t k = 0; k < len; ++k) {
+        const int64_t pos = base + k * SELL_C, t = ptr[r] + k;
+        const int32_t c = scol[pos];
+        double v[4];
+        v[3] = 0;
+        for (int i = 0; i < KI; ++i) {
+            v[i] = m[pos] + rc.tau[i] * a[pos];
+            v[3] += z[i] * e[i * ne + pos];
+        }
+        if (r == pin) v[3] = (c == r) ? 1.0 : 0.0;
+        if (c == pin && r != pin) v[3] = 0.0;
+        col[t] = c;
+        for (int f = 0; f < 4; ++f) {
+            val[4 * t + f] = v[f];
+            if (c == r) diag[4 * r + f] = v[f];
+        }
+        strength[t] = a[pos];
+    }
+}
+
+// S = sqrt(diag P_0), S^-1, and S with the pinned row left out of the stopping test's norms
+__global__ void k_p0_scaling(int64_t n4, int64_t pin4, const double* __restrict__ diag, double* __restrict__ sv,
+                             double* __restrict__ si, double* __restrict__ sw, int* __restrict__ bad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    const double d = diag[i];
+    if (!(d > 0.0) || !isfinite(d)) atomicExch(bad, 1);
+    const double r = sqrt(d);
+    sv[i] = r;
+    si[i] = 1.0 / r;
+    sw[i] = i == pin4 ? 0.0 : r;
+}
+
+// C = A B on the device. Rows whose keys overflow the shared-memory hash (more than hcap/2 of
+// them) are finished by k_spgemm_long; the number of such rows is added to *long_rows_out.
+void spgemm_gpu(const DevCsr4d& A, const DevCsr4d& B, DevCsr4d& C, cudaStream_t st, int64_t* long_rows_out,
+                int short_row_max) {
     const int64_t n = A.n_rows;
     DArray<unsigned long long> maxb;
     maxb.alloc(1);
@@ -618,23 +855,32 @@ bool spgemm_gpu(const DCsr4& A, const DCsr4& B, DCsr4& C, cudaStream_t st) {
     int64_t want = (int64_t)std::min<unsigned long long>(bound, (unsigned long long)B.n_cols);
     int hcap = 64;
     while (hcap < 2 * want + 2 && hcap < 8192) hcap <<= 1;
+    const int kcap = short_row_max > 0 ? std::min(hcap / 2, short_row_max) : hcap / 2;
     const int wpb = hcap <= 1024 ? 4 : 1;
     const size_t smem = (size_t)wpb * (2 * hcap + 1) * sizeof(int32_t);
     if (smem > 48 * 1024) {
         KNP_CUDA(cudaFuncSetAttribute(k_spgemm_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         KNP_CUDA(cudaFuncSetAttribute(k_spgemm_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    DArray<int64_t> cnt;
-    DArray<int> ovf;
+    DArray<int64_t> cnt, long_rows;
+    DArray<unsigned long long> n_long;
     cnt.alloc(n);
-    ovf.alloc(1);
-    ovf.zero(st);
+    long_rows.alloc(std::max<int64_t>(n, 1));
+    n_long.alloc(1);
+    n_long.zero(st);
     const unsigned grid = (unsigned)((n + wpb - 1) / wpb);
-    k_spgemm_count<<<grid, 32 * wpb, smem, st>>>(n, A.ptr.p, A.col.p, B.ptr.p, B.col.p, hcap, cnt.p, ovf.p);
-    int of = 0;
-    KNP_CUDA(cudaMemcpyAsync(&of, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    k_spgemm_count<<<grid, 32 * wpb, smem, st>>>(n, A.ptr.p, A.col.p, B.ptr.p, B.col.p, hcap, kcap, cnt.p, long_rows.p,
+                                                 n_long.p);
+    unsigned long long nl = 0;
+    KNP_CUDA(cudaMemcpyAsync(&nl, n_long.p, sizeof(nl), cudaMemcpyDeviceToHost, st));
     KNP_CUDA(cudaStreamSynchronize(st));
-    if (of) return false;
+    LongRowWork ws;
+    if (nl) {
+        ws.setup((int64_t)nl, B.n_cols, st);
+        k_spgemm_long<<<ws.blocks, 256, 0, st>>>((int64_t)nl, long_rows.p, B.n_cols, A.ptr.p, A.col.p, A.val.p,
+                                                 B.ptr.p, B.col.p, B.val.p, 0, cnt.p, nullptr, nullptr, nullptr,
+                                                 ws.acc.p, ws.mark.p);
+    }
     C.n_rows = n;
     C.n_cols = B.n_cols;
     C.ptr.alloc(n + 1);
@@ -642,40 +888,85 @@ bool spgemm_gpu(const DCsr4& A, const DCsr4& B, DCsr4& C, cudaStream_t st) {
     C.col.alloc(std::max<int64_t>(1, C.nnz));
     C.val.alloc(std::max<int64_t>(1, 4 * C.nnz));
     k_spgemm_fill<<<grid, 32 * wpb, smem, st>>>(n, A.ptr.p, A.col.p, A.val.p, B.ptr.p, B.col.p, B.val.p, hcap,
-                                                C.ptr.p, C.col.p, C.val.p);
+                                                kcap, C.ptr.p, C.col.p, C.val.p);
+    if (nl)
+        k_spgemm_long<<<ws.blocks, 256, 0, st>>>((int64_t)nl, long_rows.p, B.n_cols, A.ptr.p, A.col.p, A.val.p,
+                                                 B.ptr.p, B.col.p, B.val.p, 1, nullptr, C.ptr.p, C.col.p, C.val.p,
+                                                 ws.acc.p, ws.mark.p);
     KNP_CUDA(cudaGetLastError());
-    return true;
+    if (long_rows_out) *long_rows_out += (int64_t)nl;
 }
 
 }  // namespace
 
+int64_t device_exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
+    return exclusive_scan(in, out, n, st);
+}
+
+void download(const DevCsr4d& d, HostCsr4& h, cudaStream_t st) {
+    h.n_rows = d.n_rows;
+    h.n_cols = d.n_cols;
+    d.ptr.download(h.ptr, st);
+    d.col.download(h.col, st);
+    d.val.download(h.val, st);
+    h.col.resize(d.nnz);
+    h.val.resize(4 * d.nnz);
+    KNP_CUDA(cudaStreamSynchronize(st));
+}
+
+void p0_extract(knp_problem* p, DevCsr4d& A0, DArray<double>& strength) {
+    cudaStream_t st = p->stream;
+    const int64_t n = p->n_nodes;
+    const SellPattern& S = p->sell;
+    A0.n_rows = A0.n_cols = n;
+    DArray<int64_t> cnt;
+    cnt.alloc(n);
+    k_p0_count<<<nb(n, 256), 256, 0, st>>>(n, S.slice_ptr.p, S.col.p, cnt.p);
+    A0.ptr.alloc(n + 1);
+    A0.nnz = exclusive_scan(cnt.p, A0.ptr.p, n, st);
+    A0.col.alloc(std::max<int64_t>(1, A0.nnz));
+    A0.val.alloc(std::max<int64_t>(1, 4 * A0.nnz));
+    strength.alloc(std::max<int64_t>(1, A0.nnz));
+    DArray<double> diag;
+    diag.alloc(4 * n);
+    k_p0_fill<<<nb(n, 128), 128, 0, st>>>(n, p->N_i, S.slice_ptr.p, S.col.p, p->sell_m.p, p->sell_a.p, p->sell_e.p,
+                                          S.n_entries, p->sp.reg[0], p->sp.reg[1], p->sp.z[0], p->sp.z[1], p->sp.z[2],
+                                          p->pin, A0.ptr.p, A0.col.p, A0.val.p, strength.p, diag.p);
+    DArray<int> bad;
+    bad.alloc(1);
+    bad.zero(st);
+    k_p0_scaling<<<nb(4 * n, 256), 256, 0, st>>>(4 * n, 4 * (int64_t)p->pin + 3, diag.p, p->svec.p, p->sinv.p,
+                                                 p->swt.p, bad.p);
+    int hb = 0;
+    KNP_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KNP_CUDA(cudaStreamSynchronize(st));
+    KNP_REQUIRE(hb == 0, KNP_ERR_NUMERIC, "P_0 diagonal is not positive");
+}
+
 // Device version of amg_build (same algorithm and output as the host one, see amg_setup.cpp).
-bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, int64_t pin_row,
-                   const AmgSetupOpts& o, HostHierarchy& H, cudaStream_t st, void (*host_spgemm)(const HostCsr4&,
-                   const HostCsr4&, HostCsr4&)) {
+void amg_build_gpu(DevCsr4d& A0, DArray<double>& s, int64_t pin_row, const AmgSetupOpts& o, GpuHierarchy& H,
+                   cudaStream_t st, int short_row_max) {
     H.levels.clear();
-    auto A = std::make_unique<DCsr4>();
-    upload(A0h, *A, st);
-    DArray<double> s;
-    s.upload(strength0, st);
+    H.long_rows_p = H.long_rows_rap = 0;
+    const int pmax = short_row_max > 0 ? std::min(short_row_max, PMAX) : PMAX;
     DArray<double> B;
-    {
-        std::vector<double> b(4 * A0h.n_rows, 1.0);
-        if (pin_row >= 0) b[4 * pin_row + 3] = 0.0;
-        B.upload(b, st);
-    }
+    B.alloc(4 * A0.n_rows);
+    k_near_null<<<nb(4 * A0.n_rows, 256), 256, 0, st>>>(4 * A0.n_rows, pin_row >= 0 ? 4 * pin_row + 3 : -1, B.p);
     DArray<int> flag;
     flag.alloc(1);
+    auto cur = std::make_unique<GpuLevel>();
+    cur->A = std::move(A0);
     for (int lev = 0;; ++lev) {
-        const int64_t n = A->n_rows;
-        H.levels.emplace_back();
-        HostLevel& L = H.levels.back();
+        GpuLevel& L = *cur;
+        DevCsr4d& A = L.A;
+        const int64_t n = A.n_rows;
+        H.levels.push_back(std::move(cur));
         // diagonal, D^-1, Chebyshev bounds
-        DArray<double> dinv, sdiag;
-        dinv.alloc(4 * n);
+        DArray<double> sdiag;
+        L.dinv.alloc(4 * n);
         sdiag.alloc(n);
         flag.zero(st);
-        k_diag<<<nb(n, 256), 256, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, lev == 0 ? s.p : nullptr, dinv.p,
+        k_diag<<<nb(n, 256), 256, 0, st>>>(n, A.ptr.p, A.col.p, A.val.p, lev == 0 ? s.p : nullptr, L.dinv.p,
                                             sdiag.p, flag.p);
         int bad = 0;
         KNP_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -691,7 +982,7 @@ bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, in
             lam.alloc(4);
             k_power_init<<<nb(4 * n, 256), 256, 0, st>>>(4 * n, x.p);
             for (int it = 0; it < 20; ++it) {
-                k_power_step<<<pb, 256, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, dinv.p, x.p, y.p, partial.p);
+                k_power_step<<<pb, 256, 0, st>>>(n, A.ptr.p, A.col.p, A.val.p, L.dinv.p, x.p, y.p, partial.p);
                 k_power_scale<<<pb, 256, 0, st>>>(4 * n, pb, partial.p, y.p, x.p, lam.p);
             }
             double rho[4];
@@ -702,27 +993,25 @@ bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, in
                 L.lmin[f] = L.lmax[f] / o.cheb_ratio;
             }
         }
-        dinv.download(L.dinv, st);
-        download(*A, L.A, st);
         if (n <= o.coarse_max || lev + 1 >= o.max_levels) break;
         // strength graph (level 0: the given scalar; coarser: the potential field)
         const double theta = (lev == 0 || o.theta_coarse < 0) ? o.theta : o.theta_coarse;
         DArray<double> sc;
         const double* sv = s.p;
         if (lev > 0) {
-            std::vector<double> hs(A->nnz);
-            for (int64_t t = 0; t < A->nnz; ++t) hs[t] = L.A.val[4 * t + 3];
-            sc.upload(hs, st);
+            sc.alloc(std::max<int64_t>(1, A.nnz));
+            k_field3<<<nb(A.nnz, 256), 256, 0, st>>>(A.nnz, A.val.p, sc.p);
             sv = sc.p;
         }
         DArray<int64_t> cnt, gptr;
         DArray<int32_t> gadj;
         cnt.alloc(n);
         gptr.alloc(n + 1);
-        k_strength_count<<<nb(n, 256), 256, 0, st>>>(n, A->ptr.p, A->col.p, sv, sdiag.p, theta, cnt.p);
+        k_strength_count<<<nb(n, 256), 256, 0, st>>>(n, A.ptr.p, A.col.p, sv, sdiag.p, theta, cnt.p);
         int64_t ne = exclusive_scan(cnt.p, gptr.p, n, st);
         gadj.alloc(std::max<int64_t>(1, ne));
-        k_strength_fill<<<nb(n, 256), 256, 0, st>>>(n, A->ptr.p, A->col.p, sv, sdiag.p, theta, gptr.p, gadj.p);
+        k_strength_fill<<<nb(n, 256), 256, 0, st>>>(n, A.ptr.p, A.col.p, sv, sdiag.p, theta, gptr.p, gadj.p);
+        if (lev == 0) s.release();
         // MIS-2 rounds
         DArray<uint8_t> state;
         DArray<uint64_t> prio, m1, m2;
@@ -743,6 +1032,9 @@ bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, in
             KNP_CUDA(cudaStreamSynchronize(st));
             if (u == 0) break;
         }
+        m1.release();
+        m2.release();
+        prio.release();
         // aggregates
         DArray<int64_t> fl, rank;
         fl.alloc(n);
@@ -767,28 +1059,48 @@ bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, in
         int64_t extra = exclusive_scan(fl.p, rank.p, n, st);
         k_singletons<<<nb(n, 256), 256, 0, st>>>(n, na, rank.p, agg.p);
         na += extra;
+        gadj.release();
+        agg2.release();
         if (na >= n || na == 0 || (double)na > 0.85 * (double)n) break;
-        // smoothed prolongator
+        // smoothed prolongator; rows with more than pmax aggregates go to k_prolong_long
         double om[4];
         for (int f = 0; f < 4; ++f) om[f] = (4.0 / 3.0) / (L.lmax[f] / 1.1);
-        DCsr4 P;
+        DevCsr4d& P = L.P;
         P.n_rows = n;
         P.n_cols = na;
         P.ptr.alloc(n + 1);
-        flag.zero(st);
-        k_prolong<<<nb(n, 64), 64, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, dinv.p, B.p, agg.p, om[0], om[1], om[2],
-                                            om[3], o.p_drop, 0, cnt.p, nullptr, nullptr, nullptr, flag.p);
-        int of = 0;
-        KNP_CUDA(cudaMemcpyAsync(&of, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DArray<int64_t> long_rows;
+        DArray<unsigned long long> n_long;
+        long_rows.alloc(n);
+        n_long.alloc(1);
+        n_long.zero(st);
+        k_prolong<<<nb(n, 64), 64, 0, st>>>(n, A.ptr.p, A.col.p, A.val.p, L.dinv.p, B.p, agg.p, om[0], om[1], om[2],
+                                            om[3], o.p_drop, 0, cnt.p, nullptr, nullptr, nullptr, long_rows.p, n_long.p,
+                                            pmax);
+        unsigned long long nl = 0;
+        KNP_CUDA(cudaMemcpyAsync(&nl, n_long.p, sizeof(nl), cudaMemcpyDeviceToHost, st));
         KNP_CUDA(cudaStreamSynchronize(st));
-        if (of) return false;   // a row of P with more than PMAX aggregates: the caller uses the host build
+        LongRowWork ws;
+        if (nl) {
+            ws.setup((int64_t)nl, na, st);
+            k_prolong_long<<<ws.blocks, 256, 0, st>>>((int64_t)nl, long_rows.p, na, A.ptr.p, A.col.p, A.val.p,
+                                                      L.dinv.p, B.p, agg.p, om[0], om[1], om[2], om[3], o.p_drop, 0,
+                                                      cnt.p, nullptr, nullptr, nullptr, ws.acc.p, ws.mark.p);
+            H.long_rows_p += (int64_t)nl;
+        }
         P.nnz = exclusive_scan(cnt.p, P.ptr.p, n, st);
-        P.col.alloc(P.nnz);
-        P.val.alloc(4 * P.nnz);
-        k_prolong<<<nb(n, 64), 64, 0, st>>>(n, A->ptr.p, A->col.p, A->val.p, dinv.p, B.p, agg.p, om[0], om[1], om[2],
-                                            om[3], o.p_drop, 1, nullptr, P.ptr.p, P.col.p, P.val.p, flag.p);
+        P.col.alloc(std::max<int64_t>(1, P.nnz));
+        P.val.alloc(std::max<int64_t>(1, 4 * P.nnz));
+        k_prolong<<<nb(n, 64), 64, 0, st>>>(n, A.ptr.p, A.col.p, A.val.p, L.dinv.p, B.p, agg.p, om[0], om[1], om[2],
+                                            om[3], o.p_drop, 1, nullptr, P.ptr.p, P.col.p, P.val.p, long_rows.p,
+                                            n_long.p, pmax);
+        if (nl)
+            k_prolong_long<<<ws.blocks, 256, 0, st>>>((int64_t)nl, long_rows.p, na, A.ptr.p, A.col.p, A.val.p,
+                                                      L.dinv.p, B.p, agg.p, om[0], om[1], om[2], om[3], o.p_drop, 1,
+                                                      nullptr, P.ptr.p, P.col.p, P.val.p, ws.acc.p, ws.mark.p);
+        long_rows.release();
         // R = P^T
-        DCsr4 R;
+        DevCsr4d& R = L.R;
         R.n_rows = na;
         R.n_cols = n;
         R.nnz = P.nnz;
@@ -804,37 +1116,36 @@ bool amg_build_gpu(const HostCsr4& A0h, const std::vector<double>& strength0, in
             KNP_CUDA(cudaMemcpyAsync(cc64.p, cc.p, na * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
             R.ptr.alloc(na + 1);
             exclusive_scan(cc64.p, R.ptr.p, na, st);
-            R.col.alloc(R.nnz);
-            R.val.alloc(4 * R.nnz);
+            R.col.alloc(std::max<int64_t>(1, R.nnz));
+            R.val.alloc(std::max<int64_t>(1, 4 * R.nnz));
             k_transpose_fill<<<nb(n, 256), 256, 0, st>>>(n, P.ptr.p, P.col.p, P.val.p, R.ptr.p, fill.p, R.col.p,
                                                          R.val.p);
             k_sort_rows_block<<<(unsigned)na, SORT_THREADS, 0, st>>>(na, R.ptr.p, R.col.p, R.val.p);
         }
-        download(P, L.P, st);
-        download(R, L.R, st);
         // coarse near-null vectors
         DArray<unsigned long long> Bc;
         Bc.alloc(4 * na);
         Bc.zero(st);
         k_coarse_B<<<nb(n, 256), 256, 0, st>>>(n, agg.p, B.p, Bc.p);
         // Galerkin product
-        auto AP = std::make_unique<DCsr4>();
-        auto Ac = std::make_unique<DCsr4>();
-        bool ok = spgemm_gpu(*A, P, *AP, st) && spgemm_gpu(R, *AP, *Ac, st);
-        if (!ok) {
-            HostCsr4 hAP, hAc;
-            host_spgemm(L.A, L.P, hAP);
-            host_spgemm(L.R, hAP, hAc);
-            upload(hAc, *Ac, st);
+        auto next = std::make_unique<GpuLevel>();
+        {
+            DevCsr4d AP;
+            spgemm_gpu(A, P, AP, st, &H.long_rows_rap, short_row_max);
+            spgemm_gpu(R, AP, next->A, st, &H.long_rows_rap, short_row_max);
         }
         B.alloc(4 * na);
         KNP_CUDA(cudaMemcpyAsync(B.p, Bc.p, 4 * na * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        A = std::move(Ac);
         KNP_CUDA(cudaGetLastError());
+        cur = std::move(next);
     }
-    // dense inverse of the coarsest operator on the host
-    amg_coarse_inverse(H);
-    return true;
+    // dense inverse of the coarsest operator on the host (a few hundred unknowns)
+    HostHierarchy Hc;
+    Hc.levels.emplace_back();
+    download(H.levels.back()->A, Hc.levels.back().A, st);
+    amg_coarse_inverse(Hc);
+    H.coarse_inv = std::move(Hc.coarse_inv);
+    H.nc = Hc.nc;
 }
 
 }  // namespace knp

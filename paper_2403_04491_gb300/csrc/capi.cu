@@ -1,10 +1,13 @@
 // C ABI of the problem object: creation, assembly, AMG setup, solve, stepping,
 // state access and the inspection entry points (see include/knp.h).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "amg.h"
+#include "amg_gpu.h"
 #include "gmres.h"
 #include "problem.h"
 #include "vcycle.h"
@@ -184,67 +187,47 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
                     "CG(P_0) needs the FP64 hierarchy");
         if (!p->assembled) launch_assembly(p);
         cudaStream_t st = p->stream;
-        std::vector<double> m, a, e;
-        p->sell_m.download(m, st);
-        p->sell_a.download(a, st);
-        p->sell_e.download(e, st);
-        KNP_CUDA(cudaStreamSynchronize(st));
-        const SellPattern& S = p->sell;
-        const int64_t n = p->n_nodes, ne = S.n_entries;
-        // P_0: the field-diagonal blocks of A_0 (Eq. 4.4) on the region-internal pattern
-        HostCsr4 A0;
-        A0.n_rows = A0.n_cols = n;
-        A0.ptr.assign(n + 1, 0);
-        std::vector<double> strength;
-        std::vector<double> diag(4 * n, 0.0);
-        for (int64_t r = 0; r < n; ++r) {
-            const RegionCoef& rc = p->sp.reg[r < p->N_i ? 0 : 1];
-            int64_t s = r / SELL_C, base = S.h_slice_ptr[s] + r % SELL_C;
-            int64_t w = (S.h_slice_ptr[s + 1] - S.h_slice_ptr[s]) / SELL_C;
-            int32_t prev = -1;
-            for (int64_t k = 0; k < w; ++k) {
-                int64_t pos = base + k * SELL_C;
-                int32_t c = S.h_col[pos];
-                if (c <= prev) break;  // padding repeats the row id after the sorted columns
-                prev = c;
-                A0.col.push_back(c);
-                double v[4];
-                v[3] = 0;
-                for (int i = 0; i < KI; ++i) {
-                    v[i] = m[pos] + rc.tau[i] * a[pos];
-                    v[3] += p->sp.z[i] * e[i * ne + pos];
-                }
-                if (r == p->pin) v[3] = (c == r) ? 1.0 : 0.0;
-                if (c == p->pin && r != p->pin) v[3] = 0.0;
-                for (int f = 0; f < 4; ++f) {
-                    A0.val.push_back(v[f]);
-                    if (c == r) diag[4 * r + f] = v[f];
-                }
-                strength.push_back(a[pos]);
-            }
-            A0.ptr[r + 1] = (int64_t)A0.col.size();
-        }
-        std::vector<double> sv(4 * n), si(4 * n);
-        for (int64_t i = 0; i < 4 * n; ++i) {
-            KNP_REQUIRE(diag[i] > 0 && std::isfinite(diag[i]), KNP_ERR_NUMERIC, "P_0 diagonal is not positive");
-            sv[i] = std::sqrt(diag[i]);
-            si[i] = 1.0 / sv[i];
-        }
-        HostHierarchy H;
+        const auto t0 = std::chrono::steady_clock::now();
+        // P_0: the field-diagonal blocks of A_0 (Eq. 4.4) on the region-internal pattern, with the
+        // pin; also the solver's diagonal scaling S = sqrt(diag P_0)
+        DevCsr4d A0;
+        DArray<double> strength;
+        p0_extract(p, A0, strength);
         AmgSetupOpts so{o->theta, o->coarse_max, o->max_levels, o->cheb_ratio, o->theta_coarse, o->p_drop};
-        if (o->host_setup || !amg_build_gpu(A0, strength, p->pin, so, H, st, amg_host_spgemm))
-            amg_build(A0, strength, p->pin, so, H);
-        amg_upload(p, H, o->precision, o->cheb_degree);
+        if (o->host_setup) {
+            // the host C++ build of the same algorithm: a reference for the GPU build
+            HostCsr4 A0h;
+            std::vector<double> sh;
+            download(A0, A0h, st);
+            strength.download(sh, st);
+            KNP_CUDA(cudaStreamSynchronize(st));
+            sh.resize(A0.nnz);
+            A0 = DevCsr4d();
+            strength.release();
+            HostHierarchy H;
+            amg_build(A0h, sh, p->pin, so, H);
+            amg_upload(p, H, o->precision, o->cheb_degree);
+        } else {
+            const char* cap = std::getenv("KNP_AMG_SHORT_ROW_MAX");
+            GpuHierarchy G;
+            amg_build_gpu(A0, strength, p->pin, so, G, st, cap ? std::atoi(cap) : 0);
+            amg_take_gpu(p, G, o->precision, o->cheb_degree);
+        }
         p->amg->inner_cg_max_it = o->inner_cg_max_it;
         p->amg->inner_cg_rtol = o->inner_cg_rtol;
-        KNP_CUDA(cudaMemcpyAsync(p->svec.p, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        KNP_CUDA(cudaMemcpyAsync(p->sinv.p, si.data(), si.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        // the pinned row is an identity whose scale says nothing about the solution: leave it out
-        // of the norms of the stopping test
-        std::vector<double> sw = sv;
-        sw[4 * (int64_t)p->pin + 3] = 0.0;
-        KNP_CUDA(cudaMemcpyAsync(p->swt.p, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         KNP_CUDA(cudaStreamSynchronize(st));
+        p->amg->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    });
+}
+
+knp_status knp_amg_setup_info(const knp_problem* p, knp_amg_setup_record* rec) {
+    return guarded([&] {
+        KNP_REQUIRE(p && rec, KNP_ERR_INVALID_ARG, "NULL argument");
+        KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
+        rec->on_gpu = p->amg->setup_on_gpu;
+        rec->long_rows_p = p->amg->long_rows_p;
+        rec->long_rows_rap = p->amg->long_rows_rap;
+        rec->setup_ms = p->amg->setup_ms;
     });
 }
 

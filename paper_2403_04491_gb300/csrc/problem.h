@@ -27,6 +27,20 @@ struct DArray {
     DArray() = default;
     DArray(const DArray&) = delete;
     DArray& operator=(const DArray&) = delete;
+    DArray(DArray&& o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DArray& operator=(DArray&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
     ~DArray() { release(); }
     void release() {
         if (p) cudaFree(p);

@@ -14,8 +14,10 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "amg.h"
+#include "amg_gpu.h"
 #include "problem.h"
 #include "vcycle.h"
 
@@ -264,6 +266,25 @@ int pick_slots(int64_t rows, double mean_len) {
 }  // namespace
 
 template <class T>
+__global__ void k_cast(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (T)in[i];
+}
+
+// device array of T from one of doubles: taken over as it is (T = double) or cast (T = float)
+template <class T>
+void take_values(DArray<T>& out, DArray<double>& in, int64_t count, cudaStream_t st) {
+    if constexpr (std::is_same<T, double>::value) {
+        out = std::move(in);
+    } else {
+        out.alloc(std::max<int64_t>(count, 1));
+        if (count) k_cast<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, in.p, out.p);
+        KNP_CUDA(cudaStreamSynchronize(st));
+        in.release();
+    }
+}
+
+template <class T>
 struct DevCsr4 {
     int64_t n = 0;
     int slots = 1;
@@ -276,6 +297,14 @@ struct DevCsr4 {
         ptr.upload(h.ptr, st);
         col.upload(h.col, st);
         val.upload(cast_vec<T>(h.val), st);
+    }
+    // takes over a device CSR built by the GPU setup (no copy through the host)
+    void take(DevCsr4d& d, cudaStream_t st) {
+        n = d.n_rows;
+        slots = pick_slots(n, n ? (double)d.nnz / (double)n : 1.0);
+        ptr = std::move(d.ptr);
+        col = std::move(d.col);
+        take_values(val, d.val, 4 * d.nnz, st);
     }
 };
 
@@ -346,6 +375,31 @@ static void upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
     L.sval.upload(val, st);
 }
 
+// work vectors of a level and the coefficients of its Chebyshev steps (Saad's three-term
+// recurrence on [lmin, lmax])
+template <class T>
+static void level_vectors_and_coefs(AmgDev<T>& D, DevLevel<T>& L, int degree, cudaStream_t st) {
+    for (DArray<T>* v : {&L.x, &L.x2, &L.b, &L.r, &L.d}) {
+        v->alloc(4 * L.n);
+        v->zero(st);
+    }
+    std::vector<Coef4> cs(std::max(degree, 1));
+    for (int f = 0; f < 4; ++f) {
+        double th = 0.5 * (L.lmax[f] + L.lmin[f]), de = 0.5 * (L.lmax[f] - L.lmin[f]);
+        double sigma = th / de;
+        double rho0 = 1.0 / sigma;
+        cs[0].c1[f] = 0.0;
+        cs[0].c2[f] = 1.0 / th;
+        for (int k = 1; k < degree; ++k) {
+            double rho1 = 1.0 / (2.0 * sigma - rho0);
+            cs[k].c1[f] = rho1 * rho0;
+            cs[k].c2[f] = 2.0 * rho1 / de;
+            rho0 = rho1;
+        }
+    }
+    D.coef.push_back(cs);
+}
+
 template <class T>
 static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, cudaStream_t st) {
     D.degree = degree;
@@ -369,26 +423,87 @@ static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, c
             L->P.upload(HL.P, st);
             L->R.upload(HL.R, st);
         }
-        for (DArray<T>* v : {&L->x, &L->x2, &L->b, &L->r, &L->d}) {
-            v->alloc(4 * n);
-            v->zero(st);
+        level_vectors_and_coefs(D, *L, degree, st);
+        D.L.push_back(std::move(L));
+    }
+    D.nc = H.nc;
+    D.cinv.upload(H.coarse_inv, st);
+}
+
+// sliced-ELL slice widths (entries per slice) from CSR row lengths
+__global__ void k_sell_widths(int64_t n, int64_t ns, const int64_t* __restrict__ ptr, int64_t* __restrict__ w) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    int64_t m = 0;
+    for (int64_t r = s * SELL_C; r < min(n, (s + 1) * SELL_C); ++r) m = max(m, ptr[r + 1] - ptr[r]);
+    w[s] = m * SELL_C;
+}
+
+// CSR -> sliced ELL; padding repeats the (clamped) row id with zero values, as upload_sell does
+template <class T>
+__global__ void k_sell_fill(int64_t n, int64_t ns, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const int64_t* __restrict__ sp, int32_t* __restrict__ scol,
+                            T* __restrict__ sval) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= ns * SELL_C) return;
+    const int64_t s = r / SELL_C, lane = r % SELL_C;
+    const int64_t w = (sp[s + 1] - sp[s]) / SELL_C;
+    const int64_t len = r < n ? ptr[r + 1] - ptr[r] : 0;
+    for (int64_t k = 0; k < w; ++k) {
+        const int64_t pos = sp[s] + k * SELL_C + lane;
+        if (k < len) {
+            const int64_t t = ptr[r] + k;
+            scol[pos] = col[t];
+            for (int f = 0; f < 4; ++f) sval[4 * pos + f] = (T)val[4 * t + f];
+        } else {
+            scol[pos] = (int32_t)min(r, n - 1);
+            for (int f = 0; f < 4; ++f) sval[4 * pos + f] = T(0);
         }
-        // Chebyshev coefficients of each step (Saad's three-term recurrence on [lmin, lmax])
-        std::vector<Coef4> cs(std::max(degree, 1));
+    }
+}
+
+template <class T>
+static void take_sell(DevLevel<T>& L, DevCsr4d& A, cudaStream_t st) {
+    const int64_t n = A.n_rows, ns = (n + SELL_C - 1) / SELL_C;
+    DArray<int64_t> w;
+    w.alloc(std::max<int64_t>(ns, 1));
+    k_sell_widths<<<nblk(ns, 256), 256, 0, st>>>(n, ns, A.ptr.p, w.p);
+    L.sp.alloc(ns + 1);
+    const int64_t total = device_exclusive_scan(w.p, L.sp.p, ns, st);
+    L.scol.alloc(std::max<int64_t>(total, 1));
+    L.sval.alloc(std::max<int64_t>(4 * total, 1));
+    k_sell_fill<T><<<nblk(ns * SELL_C, 128), 128, 0, st>>>(n, ns, A.ptr.p, A.col.p, A.val.p, L.sp.p, L.scol.p, L.sval.p);
+    KNP_CUDA(cudaStreamSynchronize(st));
+    A.ptr.release();
+    A.col.release();
+    A.val.release();
+}
+
+// The same device hierarchy as upload_hierarchy, taken over from the GPU setup level by level
+// (each level's setup arrays are released as soon as its V-cycle copy exists)
+template <class T>
+static void take_hierarchy(AmgDev<T>& D, GpuHierarchy& H, int degree, cudaStream_t st) {
+    D.degree = degree;
+    for (auto& G : H.levels) {
+        auto L = std::make_unique<DevLevel<T>>();
+        const int64_t n = G->A.n_rows;
+        L->n = n;
+        L->nnz = G->A.nnz;
+        L->sell = (double)L->nnz / (double)std::max<int64_t>(n, 1) <= 24.0;
+        if (L->sell)
+            take_sell(*L, G->A, st);
+        else
+            L->A.take(G->A, st);
+        take_values(L->dinv, G->dinv, 4 * n, st);
         for (int f = 0; f < 4; ++f) {
-            double th = 0.5 * (L->lmax[f] + L->lmin[f]), de = 0.5 * (L->lmax[f] - L->lmin[f]);
-            double sigma = th / de;
-            double rho0 = 1.0 / sigma;
-            cs[0].c1[f] = 0.0;
-            cs[0].c2[f] = 1.0 / th;
-            for (int k = 1; k < degree; ++k) {
-                double rho1 = 1.0 / (2.0 * sigma - rho0);
-                cs[k].c1[f] = rho1 * rho0;
-                cs[k].c2[f] = 2.0 * rho1 / de;
-                rho0 = rho1;
-            }
+            L->lmax[f] = G->lmax[f];
+            L->lmin[f] = G->lmin[f];
         }
-        D.coef.push_back(cs);
+        if (G->P.n_rows) {
+            L->P.take(G->P, st);
+            L->R.take(G->R, st);
+        }
+        level_vectors_and_coefs(D, *L, degree, st);
         D.L.push_back(std::move(L));
     }
     D.nc = H.nc;
@@ -414,6 +529,32 @@ void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degre
         p->amg->h64 = D;
         upload_hierarchy(*D, H, degree, p->stream);
     }
+    KNP_CUDA(cudaStreamSynchronize(p->stream));
+}
+
+void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree) {
+    delete p->amg;
+    p->amg = new AmgHierarchy();
+    p->amg->precision = precision;
+    p->amg->levels = (int)H.levels.size();
+    p->amg->use_graphs = std::getenv("KNP_NO_GRAPHS") == nullptr;
+    p->amg->setup_on_gpu = 1;
+    p->amg->long_rows_p = H.long_rows_p;
+    p->amg->long_rows_rap = H.long_rows_rap;
+    for (auto& L : H.levels) {
+        p->amg->nodes.push_back(L->A.n_rows);
+        p->amg->nnz.push_back(L->A.nnz);
+    }
+    if (precision == KNP_PREC_FP32) {
+        auto* D = new AmgDev<float>();
+        p->amg->h32 = D;
+        take_hierarchy(*D, H, degree, p->stream);
+    } else {
+        auto* D = new AmgDev<double>();
+        p->amg->h64 = D;
+        take_hierarchy(*D, H, degree, p->stream);
+    }
+    H.levels.clear();
     KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 
@@ -746,6 +887,14 @@ extern "C" knp_status knp_apply_preconditioner_noalloc(knp_problem* p, const dou
     return guarded([&] {
         KNP_REQUIRE(p && r && z, KNP_ERR_INVALID_ARG, "NULL argument");
         KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
+        // the static array is looked up on the current device: it must be the problem's
+        cudaPointerAttributes at{};
+        KNP_CUDA(cudaPointerGetAttributes(&at, p->u.p));
+        int dev = -1;
+        KNP_CUDA(cudaGetDevice(&dev));
+        KNP_REQUIRE(at.device == dev, KNP_ERR_INVALID_ARG,
+                    "the current device (%d) is not the problem's device (%d); make it current first", dev,
+                    at.device);
         if (p->amg->h32)
             na_apply(p, *static_cast<AmgDev<float>*>(p->amg->h32), r, z);
         else

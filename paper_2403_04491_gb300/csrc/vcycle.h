@@ -29,10 +29,18 @@ struct AmgHierarchy {
     int inner_cg_max_it = 0;
     double inner_cg_rtol = 0.0;
     int64_t inner_its = 0;   // inner CG iterations so far
+    // how the hierarchy was built: on the GPU (1) or on the host (0, host_setup), and the rows
+    // of P and of the Galerkin products that the GPU setup finished with its long-row kernels
+    int setup_on_gpu = 0;
+    int64_t long_rows_p = 0, long_rows_rap = 0;
+    double setup_ms = 0.0;
     ~AmgHierarchy();
 };
 
 void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degree);
+struct GpuHierarchy;
+// the hierarchy built by amg_build_gpu, taken over on the device (consumes H)
+void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree);
 void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z);
 // y = P_0 x with the finest level of the FP64 hierarchy; x, y [n][4] doubles on the device
 void p0_apply(knp_problem* p, const double* x, double* y);

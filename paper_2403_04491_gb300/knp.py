@@ -71,6 +71,11 @@ class AmgOpts(C.Structure):
                 ("inner_cg_max_it", C.c_int32), ("inner_cg_rtol", C.c_double)]
 
 
+class AmgSetupRecord(C.Structure):
+    _fields_ = [("on_gpu", C.c_int32), ("long_rows_p", C.c_int64), ("long_rows_rap", C.c_int64),
+                ("setup_ms", C.c_double)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32), ("phi_e_group", C.c_int32)]
 
@@ -118,6 +123,7 @@ SIGNATURES = {
     "knp_apply_preconditioner": [C.c_void_p, _DP, _DP],
     "knp_apply_preconditioner_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p],
     "knp_amg_info": [C.c_void_p, _IP, _LP, _LP, _DP],
+    "knp_amg_setup_info": [C.c_void_p, C.c_void_p],
     "knp_problem_get_info": [C.c_void_p, C.c_void_p],
     "knp_problem_set_facet_gleak": [C.c_void_p, C.c_int32, C.c_void_p],
     "knp_adjoint_begin": [C.c_void_p],
@@ -465,6 +471,13 @@ class Problem:
         _check(_lib.knp_amg_info(self.handle, C.byref(lv), _lptr(nodes), _lptr(nnz), C.byref(oc)))
         return {"levels": lv.value, "nodes": nodes[:lv.value].tolist(), "nnz": nnz[:lv.value].tolist(),
                 "op_complexity": oc.value}
+
+    def amg_setup_info(self):
+        """How the hierarchy was built: on the GPU or the host, the rows finished by the long-row
+        kernels, and the setup's wall time."""
+        r = AmgSetupRecord()
+        _check(_lib.knp_amg_setup_info(self.handle, C.byref(r)))
+        return {f: getattr(r, f) for f, _ in AmgSetupRecord._fields_}
 
     def info(self):
         i = ProblemInfo()

@@ -83,6 +83,40 @@ def test_time_steps_match_oracle(name, n_steps, exact, precision):
         assert abs(s["t"] - n * cfg.dt) < 1e-15
 
 
+_HORIZON = {}
+
+
+def _horizon_ref():
+    """Oracle states of the 64^3 HH workload's scenario on its 24^3 mesh for 26 steps (LU(P_0)-GMRES
+    to 1e-14): the stimulus ends at t = 1 ms, after step 20."""
+    if "ref" not in _HORIZON:
+        _HORIZON["ref"] = oracle_run(make_config(2).with_nx(24), 26, "lu_p0")
+    return _HORIZON["ref"]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64-amg", "fp32-amg"])
+def test_config2_horizon_past_the_stimulus(precision):
+    """The 3D HH workload (one cell, stimulus 40 S/m^2 on facets with x < 0.4 L for t < 1 ms,
+    dt 0.05 ms) on its 24^3 mesh for 26 steps, so that the run crosses the end of the stimulus at
+    step 20 and the HH upstroke it drives: every step matches the oracle at 1e-8 (rtol 1e-10)."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2).with_nx(24)
+    pb, ref = _horizon_ref()
+    _, prob = problem_from_config(cfg)
+    prob.amg_setup(precision=precision)
+    phim = []
+    for n in range(1, 27):
+        prob.step(1, rtol=1e-10)
+        s = prob.state_get()
+        ec, ep = rel_errors(s, ref[n])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep)
+        np.testing.assert_allclose(s["w"], ref[n].w, rtol=TOL, atol=1e-12)
+        phim.append(float(np.mean(ref[n].phi_i)))
+    # the run does cross an upstroke: the intracellular potential rises by more than 10 mV
+    assert max(phim) - phim[0] > 10e-3, phim
+
+
 @pytest.mark.slow
 def test_config3_subset_125_cells_mixed():
     """The 125-cell workload at its 32^3 version (192,748 unknowns), FP32 hierarchy, 3 steps."""
@@ -160,6 +194,7 @@ def test_gpu_amg_setup_matches_host_setup(precision):
     b.amg_setup(precision=precision, host_setup=False)
     ia, ib = a.amg_info(), b.amg_info()
     assert ia["nodes"] == ib["nodes"] and ia["nnz"] == ib["nnz"], (ia, ib)
+    assert a.amg_setup_info()["on_gpu"] == 0 and b.amg_setup_info()["on_gpu"] == 1
     r = np.random.default_rng(9).standard_normal(a.n_dof)
     za, zb = a.apply_preconditioner(r), b.apply_preconditioner(r)
     tol = 1e-10 if precision == 0 else 1e-5
@@ -167,6 +202,49 @@ def test_gpu_amg_setup_matches_host_setup(precision):
     sa = a.step(2, rtol=1e-10)
     sb = b.step(2, rtol=1e-10)
     assert [s["iterations"] for s in sa] == [s["iterations"] for s in sb]
+
+
+@pytest.mark.parametrize("cap", [4, 24])
+def test_gpu_amg_long_rows_match_host_setup(cap, monkeypatch):
+    """Rows of the smoothed prolongator and of the Galerkin products that do not fit the short-row
+    kernels (more than 96 aggregates in a row of P, more keys in a row of A P or R A P than the
+    shared-memory hash holds) are finished on the GPU by the dense long-row kernels, with no host
+    fallback. Lowering the short-row capacity sends many rows down that path; the hierarchy must
+    still equal the host build's."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2).with_nx(24)
+    _, a = problem_from_config(cfg)
+    a.amg_setup(host_setup=True)
+    monkeypatch.setenv("KNP_AMG_SHORT_ROW_MAX", str(cap))
+    _, b = problem_from_config(cfg)
+    b.amg_setup(host_setup=False)
+    rec = b.amg_setup_info()
+    assert rec["on_gpu"] == 1 and rec["long_rows_rap"] > 0, rec
+    if cap == 4:
+        assert rec["long_rows_p"] > 0, rec   # no row of P has more than 24 aggregates here
+    ia, ib = a.amg_info(), b.amg_info()
+    assert ia["nodes"] == ib["nodes"] and ia["nnz"] == ib["nnz"], (ia, ib)
+    r = np.random.default_rng(9).standard_normal(a.n_dof)
+    za, zb = a.apply_preconditioner(r), b.apply_preconditioner(r)
+    assert np.linalg.norm(za - zb) <= 1e-10 * np.linalg.norm(za)
+
+
+@pytest.mark.parametrize("cfg_id,nx", [(2, 64), (3, 128)])
+def test_gpu_amg_setup_at_scale(cfg_id, nx):
+    """At the 64^3 workload (1.1M unknowns) and the 125-cell 128^3 workload (9.3M unknowns) the
+    hierarchy is built on the GPU (no host build), level sizes shrink, and one V-cycle of the FP32
+    hierarchy on a smooth vector is finite."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(cfg_id).with_nx(nx)
+    _, prob = problem_from_config(cfg)
+    prob.amg_setup(precision=1)
+    rec = prob.amg_setup_info()
+    info = prob.amg_info()
+    print(cfg.name, rec, info)
+    assert rec["on_gpu"] == 1
+    assert all(b < a for a, b in zip(info["nodes"], info["nodes"][1:])) and info["nodes"][-1] <= 8192
+    z = prob.apply_preconditioner(np.ones(prob.n_dof))
+    assert np.all(np.isfinite(z))
 
 
 @pytest.mark.parametrize("name", ["cfg2-3d-hh-16", "kir-3d-16"])
