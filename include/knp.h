@@ -266,7 +266,20 @@ typedef struct {
     int32_t max_it;    /* total iterations */
     int32_t phi_e_group;  /* 1: test the extracellular potentials as a third group (phi_e is some 1e-8
                              of phi_i; a loss built on phi_e needs it resolved on its own scale) */
+    int32_t deflate;      /* 1: wrap P_0^{-1} in a coarse correction of the potentials' near-null modes
+                             (each cell's constant phi_i, the constant phi_e; E = Z^T A Z solved
+                             exactly). The potential blocks of P_0 are held only by the membrane
+                             capacitance and the point pin, so one V-cycle amplifies residuals along
+                             these modes; the paper's left-preconditioned GMRES minimises exactly that
+                             amplified residual, right-preconditioned FGMRES needs the correction to
+                             converge in the same norm. Forward solves only (ignored for A^T). */
+    int32_t stop_test;    /* KNP_TEST_SCALED (0): the per-group scaled test above. KNP_TEST_PAPER (1):
+                             the test of the paper's solver settings (Section 6.2),
+                             ||M^-1 r||_2 <= rtol ||M^-1 f||_2 over the whole unscaled vector, for
+                             comparing iteration counts with Tables 3 and 4 */
 } knp_solve_opts;
+
+enum { KNP_TEST_SCALED = 0, KNP_TEST_PAPER = 1 };
 
 typedef struct {
     int32_t iterations;
@@ -357,6 +370,12 @@ knp_status knp_operator_entries(knp_problem* prob, int64_t count, const int64_t*
                                 const int64_t* cols, double* vals);
 /* z = V-cycle(P_0) r (one application of the preconditioner, unscaled); host [n]. */
 knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* z);
+/* z = M_D^{-1} r: the preconditioner of knp_solve with deflate = 1, P_0^{-1} wrapped in the coarse
+ * correction of the potentials' near-null modes (each cell's constant phi_i and the constant
+ * phi_e): y = E^{-1} Z^T r with E = Z^T A_{n-1} Z, z = V-cycle(P_0)(r - A_{n-1} Z y) + Z y, on the
+ * operator of the current assembly. Host [n] arrays in the Eq. 4.3 order. Errors:
+ * KNP_ERR_INVALID_ARG, KNP_ERR_STATE (no hierarchy or no assembled step), KNP_ERR_CUDA. */
+knp_status knp_apply_deflated_preconditioner(knp_problem* prob, const double* r, double* z);
 /* Allocation-free variant of knp_apply_preconditioner. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc when they need the
  * preconditioner - code running under a CUDA stream capture or while a CUDA graph is being

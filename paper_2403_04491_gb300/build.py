@@ -12,7 +12,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libknp.so")
 SOURCES = ["topology.cpp", "amg_setup.cpp", "problem.cu", "assemble.cu", "spmv.cu", "vcycle.cu", "gmres.cu",
            "capi.cu", "profile.cu", "adjoint.cu", "amg_gpu.cu",
-           "pcg.cu", "p2_tables.cpp"]
+           "pcg.cu", "p2_tables.cpp", "deflate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -446,6 +446,7 @@ double stimulus_at(const knp_problem_desc& d, double t) {
 }
 
 void launch_assembly(knp_problem* P) {
+    P->assembly_id++;
     if (P->degree == 2) {
         launch_assembly_p2(P);
         return;

@@ -8,6 +8,7 @@
 
 #include "amg.h"
 #include "amg_gpu.h"
+#include "deflate.h"
 #include "gmres.h"
 #include "problem.h"
 #include "vcycle.h"
@@ -66,6 +67,7 @@ knp_problem::~knp_problem() {
     gmres_free(gw);
     adjoint_free(adj);
     pcg_free(pcg);
+    deflation_free(defl);
 }
 
 extern "C" {
@@ -413,6 +415,25 @@ knp_status knp_apply_preconditioner(knp_problem* p, const double* r, double* z) 
         d1.upload(ones, p->stream);
         dz.alloc(ri.size());
         vcycle_apply(p, dr.p, d1.p, dz.p);
+        dz.download(zi, p->stream);
+        KNP_CUDA(cudaStreamSynchronize(p->stream));
+        from_interleaved(p, zi, z);
+    });
+}
+
+knp_status knp_apply_deflated_preconditioner(knp_problem* p, const double* r, double* z) {
+    return guarded([&] {
+        KNP_REQUIRE(p && r && z, KNP_ERR_INVALID_ARG, "NULL argument");
+        KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
+        KNP_REQUIRE(p->assembled, KNP_ERR_STATE, "no assembled step");
+        std::vector<double> ri, zi(4 * p->n_nodes), ones(4 * p->n_nodes, 1.0);
+        to_interleaved(p, r, ri);
+        DArray<double> dr, dz, d1;
+        dr.upload(ri, p->stream);
+        d1.upload(ones, p->stream);
+        dz.alloc(ri.size());
+        deflation_prepare(p);
+        deflated_precond_apply(p, dr.p, d1.p, dz.p);
         dz.download(zi, p->stream);
         KNP_CUDA(cudaStreamSynchronize(p->stream));
         from_interleaved(p, zi, z);

@@ -103,6 +103,7 @@ struct AmgHierarchy;        // vcycle.cu
 struct GmresWork;           // gmres.cu
 struct AdjointWork;         // adjoint.cu
 struct PcgWork;             // pcg.cu
+struct Deflation;           // deflate.cu
 
 }  // namespace knp
 
@@ -173,6 +174,8 @@ struct knp_problem {
     knp::GmresWork* gw = nullptr;
     knp::AdjointWork* adj = nullptr;
     knp::PcgWork* pcg = nullptr;
+    knp::Deflation* defl = nullptr;   // coarse correction of the potentials' near-null modes
+    int64_t assembly_id = 0;          // assemblies so far (the correction's data follow the operator)
     ~knp_problem();
 };
 

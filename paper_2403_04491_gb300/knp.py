@@ -19,6 +19,7 @@ STATUS = {0: "KNP_OK", 1: "KNP_ERR_INVALID_ARG", 2: "KNP_ERR_INVALID_MESH", 3: "
           5: "KNP_ERR_NOT_CONVERGED", 6: "KNP_ERR_NUMERIC", 7: "KNP_ERR_STATE"}
 KNP_HOST, KNP_DEVICE = 0, 1
 KNP_PREC_FP64, KNP_PREC_FP32 = 0, 1
+KNP_TEST_SCALED, KNP_TEST_PAPER = 0, 1
 MAX_IONS = 4
 
 _lib = None
@@ -77,7 +78,8 @@ class AmgSetupRecord(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32), ("phi_e_group", C.c_int32)]
+    _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32), ("phi_e_group", C.c_int32),
+                ("deflate", C.c_int32), ("stop_test", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -121,6 +123,7 @@ SIGNATURES = {
     "knp_apply_operator": [C.c_void_p, _DP, _DP],
     "knp_operator_entries": [C.c_void_p, C.c_int64, _LP, _LP, _DP],
     "knp_apply_preconditioner": [C.c_void_p, _DP, _DP],
+    "knp_apply_deflated_preconditioner": [C.c_void_p, _DP, _DP],
     "knp_apply_preconditioner_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p],
     "knp_amg_info": [C.c_void_p, _IP, _LP, _LP, _DP],
     "knp_amg_setup_info": [C.c_void_p, C.c_void_p],
@@ -352,15 +355,18 @@ class Problem:
                     int(host_setup), int(inner_cg_max_it), float(inner_cg_rtol))
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
-    def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
+    def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False, deflate=True, stop_test=KNP_TEST_SCALED):
+        """deflate: the coarse correction of the potentials' near-null modes around P_0^{-1};
+        stop_test: KNP_TEST_SCALED (per-group scaled test) or KNP_TEST_PAPER (Section 6.2's)."""
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), int(stop_test))
         s = SolveStats()
         _check(_lib.knp_solve(self.handle, C.byref(o), C.byref(s)))
         return {"iterations": s.iterations, "restarts": s.restarts, "true_relres": s.true_relres, "ms": s.ms,
                 "inner_iterations": s.inner_iterations}
 
-    def step(self, nsteps=1, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False):
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
+    def step(self, nsteps=1, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False, deflate=True,
+             stop_test=KNP_TEST_SCALED):
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), int(stop_test))
         st = (StepStats * max(nsteps, 1))()
         _check(_lib.knp_step(self.handle, nsteps, C.byref(o), st))
         return [{"iterations": st[i].iterations, "true_relres": st[i].true_relres} for i in range(nsteps)]
@@ -422,7 +428,7 @@ class Problem:
 
     def adjoint_step(self, u_n, dLdu_n, rtol=1e-10, restart=30, max_it=1000, phi_e_group=True):
         """u_n, dLdu_n in the Eq. 4.3 order: numpy arrays (host) or CUDA tensors (device)."""
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group))
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), 0, KNP_TEST_SCALED)
         s = SolveStats()
         if hasattr(u_n, "data_ptr"):
             _check(_lib.knp_adjoint_step(self.handle, KNP_DEVICE, C.c_void_p(u_n.data_ptr()),
@@ -455,6 +461,13 @@ class Problem:
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.empty(self.n_dof)
         _check(_lib.knp_apply_preconditioner(self.handle, _dptr(r), _dptr(z)))
+        return z
+
+    def apply_deflated_preconditioner(self, r):
+        """M_D^{-1} r (knp_apply_deflated_preconditioner), host arrays in the Eq. 4.3 order."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.empty(self.n_dof)
+        _check(_lib.knp_apply_deflated_preconditioner(self.handle, _dptr(r), _dptr(z)))
         return z
 
     def apply_preconditioner_noalloc(self, r_dev, z_dev):
