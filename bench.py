@@ -1,13 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark of the KNP-EMI time step (membrane update + assembly + AMG-preconditioned FGMRES).
 
-Workload: the 3D Hodgkin-Huxley scenario on the 64^3 Kuhn mesh of a 100 um cube with one
-box cell [0.3, 0.7]^3 (1,114,732 unknowns), stimulus 40 S/m^2 on facets with x < 40 um for
-t < 1 ms, dt = 0.05 ms, FGMRES(30) rtol 1e-10, FP64 hierarchy. One "step" is one IMEX time
-step; the metric is unknowns x time steps per second. AMG setup (once per run, on P_0) and
-topology are excluded, as the paper's "initialization" is; they are reported separately.
+Default workload: the large mixed-precision scenario, a 256^3 Kuhn mesh of a 100 um cube with an
+8 x 8 x 8 array of box cells (side 0.08 L with seeded +-20% jitter, gap 0.03 L), Hodgkin-Huxley
+membrane, stimulus 40 S/m^2 on facets with x < 40 um for t < 1 ms, dt = 0.05 ms: 73,078,172
+unknowns; AMG hierarchy and V-cycle in FP32 under FP64 FGMRES(30), rtol 1e-8. One "step" is one
+IMEX time step; the metric is unknowns x time steps per second. AMG setup (once per run, on P_0)
+and topology are excluded, as the paper's "initialization" is; they are reported separately.
+Other workloads with --config (2: the 64^3 one-cell FP64 scenario at rtol 1e-10; see --help).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--config C] [--impl reference]
 
 Under torchrun (N > 1) every rank runs an independent replica (the path does not shard on
 this single-GPU pool); value = unknowns x steps of all ranks / max time over ranks.
@@ -15,6 +17,7 @@ this single-GPU pool); value = unknowns x steps of all ranks / max time over ran
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -29,9 +32,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOF*timesteps/s (assembly+AMG-GMRES)"
 UNIT = "DOF*steps/s"
-WORKLOAD = "3D HH, 64^3 Kuhn tets, 100 um cube, cell [0.3,0.7]^3, 1,114,732 DOF, dt 0.05 ms, rtol 1e-10"
 PROFILE_FILE = os.path.join(ROOT, "profiles", "roofline_counters.json")
-SAMPLE_NX = 24   # oracle sample: the same scenario on the 24^3 version of its mesh
+# workloads whose unknowns exceed this run their secondary passes (profiled kernels, end to end,
+# precision comparison) over a few steps of the same window instead of all --steps
+LARGE_DOF = 20_000_000
+AUX_STEPS_LARGE = 3
+
+# CPU oracle samples per workload: (workload whose scenario the oracle runs, mesh resolution or
+# None for the workload's own). The large workloads' cell layouts cannot be coarsened much (their
+# cells would touch), so the 512-cell workload takes the 125-cell scenario at 32^3 (192,748
+# unknowns), the subset the oracle checks for the mixed-precision workloads.
+ORACLE_SAMPLE = {1: (1, None), 2: (2, 24), 3: (3, 32), 4: (4, 64), 5: (3, 32), 6: (6, 24), 7: (7, None),
+                 8: (8, 12)}
 
 
 def parse():
@@ -40,15 +52,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="hierarchy precision (default: fp32 for the mixed-precision workloads 3 and 5, else fp64)")
+    ap.add_argument("--rtol", type=float, default=None, help="FGMRES tolerance (default: the workload's)")
+    ap.add_argument("--no-deflate", action="store_true",
+                    help="solve without the coarse correction of the potentials' near-null modes")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5, 6, 7, 8],
-                    help="workload: 2 (default, the headline), 1 (2D leak), 3 (125-cell 3D, FP32 hierarchy, "
-                         "rtol 1e-8), 4 (16-cell 2D), 5 (512-cell 256^3, FP32 hierarchy, rtol 1e-8), "
-                         "6 (Kir-Na/K 64^3 with a K bolus), 7 (Kir-Na/K 2D), 8 (3D HH, interface-refined grid)")
+    ap.add_argument("--config", type=int, default=5, choices=[1, 2, 3, 4, 5, 6, 7, 8],
+                    help="workload: 5 (default: 512-cell 256^3, FP32 hierarchy, rtol 1e-8), 2 (64^3 HH, one "
+                         "cell, FP64, rtol 1e-10), 1 (2D leak), 3 (125-cell 128^3, FP32 hierarchy, rtol 1e-8), "
+                         "4 (16-cell 2D), 6 (Kir-Na/K 64^3 with a K bolus), 7 (Kir-Na/K 2D), 8 (3D HH, "
+                         "interface-refined grid)")
     ap.add_argument("--nx", type=int, default=None, help="override the mesh resolution of the workload")
     ap.add_argument("--degree", type=int, default=1, choices=[1, 2],
                     help="polynomial degree of the Lagrange elements (2: P2, Section 3.3; with --nx 32 the 3D "
@@ -56,10 +72,12 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time a checkpointed forward + adjoint run of the 16-cell 2D workload (KNPFunction)")
     args = ap.parse_args()
-    if args.config in (3, 5) and "--precision" not in sys.argv:
-        args.precision = "fp32"
-    if args.config in (3, 5) and "--rtol" not in sys.argv:
-        args.rtol = 1e-8
+    from synth import make_config
+    cfg = make_config(args.config)
+    if args.precision is None:
+        args.precision = "fp32" if cfg.mixed else "fp64"
+    if args.rtol is None:
+        args.rtol = cfg.rtol
     return args
 
 
@@ -78,49 +96,88 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 from synth import make_config
 from oracle import problem, solve, step, system
-cfg = make_config(2).with_nx({nx})
+cfg = make_config({cfg_id})
+if {nx} is not None:
+    cfg = cfg.with_nx({nx})
 t0 = time.perf_counter()
 pb, s = problem.from_config(cfg, degree={degree})
-M = solve.lu_P0(system.preconditioner_P0(pb, s))
+kw = {{}}
+if cfg.dim == 3:
+    off_i, off_e, N = system.offsets(pb)
+    kw = dict(method="gmres", M=solve.block_lu_P0(system.preconditioner_P0(pb, s), off_i + off_e + [N]), rtol=1e-13)
 t_setup = time.perf_counter() - t0
 for _ in range({warmup}):
-    s, _ = step.step(pb, s, method="gmres", M=M, rtol=1e-13)
+    s, _ = step.step(pb, s, **kw)
 times = []
 for _ in range({steps}):
     t = time.perf_counter()
-    s, _ = step.step(pb, s, method="gmres", M=M, rtol=1e-13)
+    s, _ = step.step(pb, s, **kw)
     times.append(time.perf_counter() - t)
-print(json.dumps(dict(n_dof=int(pb.topo.n_dof(3)), setup_s=t_setup, times=times)))
+print(json.dumps(dict(n_dof=int(system.offsets(pb)[2]), setup_s=t_setup, times=times)))
 """
 
 
-def run_oracle(steps, warmup, nx=SAMPLE_NX, degree=1):
+def host_cores():
+    """Host cores this process may run on (sched_getaffinity), for the CPU oracle replicas."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_replicas(cfg_id, nx, steps, warmup, degree=1, mem_per_replica_gb=6.0):
+    """The oracle on every host core at once: one single-threaded process per core, each solving
+    the same sample; the rate counts the unknowns x steps of all of them over the slowest one's
+    time. Returns (value, cores, n_dof, per-step seconds of the slowest replica)."""
+    cores = host_cores()
+    try:
+        mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 1e9
+        cores = max(1, min(cores, int(0.7 * mem_gb / mem_per_replica_gb)))
+    except (ValueError, OSError, AttributeError):
+        pass
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SNIPPET.format(root=ROOT, nx=nx, steps=steps, warmup=warmup, degree=degree)
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg_id=cfg_id, nx=nx, steps=steps, warmup=warmup, degree=degree)
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for _ in range(cores)]
+    outs = []
+    for pr in procs:
+        o, e = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(f"oracle replica failed: {e[-2000:]}")
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    slowest = max(outs, key=lambda r: sum(r["times"]))
+    n_dof = outs[0]["n_dof"]
+    value = n_dof * steps * len(outs) / sum(slowest["times"])
+    return value, len(outs), n_dof, slowest["times"]
 
 
-def oracle_sample_desc(nx, steps, degree=1):
+def oracle_sample_desc(cfg_id, nx, steps, warmup, cores, n_dof, degree=1):
+    from synth import make_config
+    cfg = make_config(cfg_id)
+    res = f"{nx}^{cfg.dim}" if nx else f"{cfg.nx}^{cfg.dim}"
     el = "" if degree == 1 else " with P2 elements"
-    return (f"oracle (numpy/scipy FP64, 1 thread) on the same scenario at {nx}^3{el} (same cell, stimulus, dt); "
-            f"{steps} steps of assembly + GMRES(30) with LU(P_0) to 1e-13, after 1 untimed step")
+    solver = ("GMRES(30) with the exact LU(P_0) to 1e-13" if cfg.dim == 3 else "sparse LU with refinement")
+    return (f"oracle (numpy/scipy FP64) on {cfg.name} at {res}{el} ({n_dof:,} unknowns), {cores} single-threaded "
+            f"replicas at once, one per host core; {steps} steps of assembly + {solver} each, after {warmup} "
+            f"untimed; rate = all replicas' unknowns x steps / the slowest replica's time")
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    r = run_oracle(args.steps, args.warmup)
-    tot = sum(r["times"])
-    value = r["n_dof"] * len(r["times"]) / tot
+    cfg_id, nx = ORACLE_SAMPLE[args.config]
+    value, cores, n_dof, times = oracle_replicas(cfg_id, nx, args.steps, args.warmup)
+    from synth import make_config
+    cfg = make_config(args.config)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=1e3 * tot / len(r["times"]), higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD + f" (oracle sample at {SAMPLE_NX}^3, {r['n_dof']} DOF)"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                                  sample=oracle_sample_desc(SAMPLE_NX, args.steps)),
+                ms_per_step=1e3 * sum(times) / len(times), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=f"{cfg.name} (oracle sample: {make_config(cfg_id).name} at "
+                                     f"{nx or make_config(cfg_id).nx}, {n_dof:,} DOF)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                                  sample=oracle_sample_desc(cfg_id, nx, args.steps, args.warmup, cores, n_dof)),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -242,7 +299,7 @@ def spmv_work(prob):
     return nnz * (4 + 40) + nx * (4 + 24) + n * 3 * 32, 18.0 * nnz + 6.0 * nx + 20.0 * n
 
 
-def measure(prob, torch, steps, rtol, kernel_class=None):
+def measure(prob, torch, steps, rtol, kernel_class=None, deflate=True):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     from paper_2403_04491_gb300.knp import launch_count
@@ -253,7 +310,7 @@ def measure(prob, torch, steps, rtol, kernel_class=None):
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(steps):
-        iters.append(prob.step(1, rtol=rtol)[0]["iterations"])
+        iters.append(prob.step(1, rtol=rtol, deflate=deflate)[0]["iterations"])
     e1.record(stream)
     torch.cuda.synchronize()
     launches = launch_count() - l0
@@ -314,113 +371,108 @@ def ours(args):
     if args.nx:
         cfg = cfg.with_nx(args.nx)
     prec = 0 if args.precision == "fp64" else 1
+    defl = not args.no_deflate
     t0 = time.perf_counter()
     mesh, prob = problem_from_config(cfg, degree=args.degree)
     t_create = time.perf_counter() - t0
     t0 = time.perf_counter()
     prob.amg_setup(precision=prec)
     t_amg = time.perf_counter() - t0
+    amg_rec = prob.amg_setup_info()
     n_dof = prob.n_dof
-    free, total = torch.cuda.mem_get_info()
-    mem_gb = (total - free) / 1e9
+    aux = args.steps if n_dof <= LARGE_DOF else min(args.steps, AUX_STEPS_LARGE)
     for _ in range(args.warmup):
-        prob.step(1, rtol=args.rtol)
+        prob.step(1, rtol=args.rtol, deflate=defl)
     torch.cuda.synchronize()
-    # every measured pass (timed, the two profiled ones, end to end) solves the same steps: the
-    # state at the start of the window is restored before each, so iteration counts match
+    # every measured pass (timed, the two profiled ones, end to end) solves steps of the same
+    # window: the state at its start is restored before each, so iteration counts match
     window = prob.state_get()
 
-    def rewind():
-        prob.state_set(window["c_i"], window["phi_i"], window["c_e"], window["phi_e"], window["w"], window["t"])
+    def rewind(pr):
+        pr.state_set(window["c_i"], window["phi_i"], window["c_e"], window["phi_e"], window["w"], window["t"])
 
     if world > 1:
         dist.barrier()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ms, iters, launches, _ = measure(prob, torch, args.steps, args.rtol)
+    ms, iters, launches, _ = measure(prob, torch, args.steps, args.rtol, deflate=defl)
     clocks = sampler.stop()
+    mem_gb = device_memory_gb(torch)
     # the reported kernels, timed by per-launch CUDA events on their stream over further passes of
-    # the same steps (event pairs go around single launches, so the V-cycle and the Arnoldi steps
-    # are not replayed from CUDA graphs in these passes)
-    rewind()
-    _, _, _, prof = measure(prob, torch, args.steps, args.rtol, kernel_class=1)
-    rewind()
-    _, _, _, prof_spmv = measure(prob, torch, args.steps, args.rtol, kernel_class=0)
-    rewind()
+    # the window's first `aux` steps (event pairs go around single launches, so the V-cycle and
+    # the Arnoldi steps are not replayed from CUDA graphs in these passes)
+    rewind(prob)
+    _, _, _, prof = measure(prob, torch, aux, args.rtol, kernel_class=1, deflate=defl)
+    rewind(prob)
+    _, it_spmv, _, prof_spmv = measure(prob, torch, aux, args.rtol, kernel_class=0, deflate=defl)
+    rewind(prob)
     ms = slowest_rank_ms(ms, world, "cuda")
+    # end to end through the public API with host buffers: per step the state goes host->device
+    # inside knp_state_set(KNP_HOST), one knp_step runs, and knp_state_get(KNP_HOST) brings it back
+    e2e = None if args.no_e2e else e2e_run(prob, torch, args, n_dof, world, window, aux, defl)
+    rewind(prob)
+    work = dict(spmv=spmv_work(prob), cheb=dominant_kernel_work(prob, args.precision), amg=prob.amg_info())
+    mixed = None
+    if not args.no_mixed and args.degree == 1 and args.config in (2, 3, 5):
+        mixed = mixed_run(cfg, mesh, prob, torch, args, n_dof, window, aux, defl)
+    prob.close()
+    report(args, work, world, rank, ms, iters, launches, (prof, prof_spmv, aux), clocks, e2e, mixed, n_dof,
+           t_create, t_amg, amg_rec, workload_name(cfg, n_dof, args.degree), mem_gb, defl)
 
-    # end to end through the public API with host buffers: per step the state goes host->device,
-    # one knp_step runs, and the new state comes back device->host (pinned host memory)
-    e2e = None if args.no_e2e else e2e_run(prob, torch, args, n_dof, world)
-    mixed = None if (args.no_mixed or args.config != 2 or args.degree != 1) else mixed_run(cfg, mesh, torch, args,
-                                                                                            n_dof)
-    report(args, prob, world, rank, ms, iters, launches, (prof, prof_spmv), clocks, e2e, mixed, n_dof, t_create, t_amg,
-           workload_name(cfg, n_dof, args.degree), mem_gb)
 
-
-def e2e_run(prob, torch, args, n_dof, world):
+def e2e_run(prob, torch, args, n_dof, world, window, steps, defl):
     import numpy as np
-    import torch.distributed as dist
-    st = prob.state_get()
-    host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory() for k in ("c_i", "phi_i", "c_e", "phi_e", "w")}
-    dev = {k: torch.empty(v.shape, dtype=torch.float64, device="cuda") for k, v in host.items()}
+    from paper_2403_04491_gb300 import knp as K
+    host = {k: torch.from_numpy(np.ascontiguousarray(window[k])).pin_memory() for k in ("c_i", "phi_i", "c_e", "phi_e", "w")}
     h2d = sum(v.numel() * 8 for v in host.values())
+    ptr = lambda tt: ctypes.cast(ctypes.c_void_p(tt.data_ptr()), K._DP)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    from paper_2403_04491_gb300 import knp as K
-    import ctypes as C
+    t = ctypes.c_double(window["t"])
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
-        for k in host:
-            dev[k].copy_(host[k], non_blocking=True)
-        ptr = lambda tt: C.cast(C.c_void_p(tt.data_ptr()), K._DP)
-        K._check(K._lib.knp_state_set(prob.handle, K.KNP_DEVICE, ptr(dev["c_i"]), ptr(dev["phi_i"]), ptr(dev["c_e"]),
-                                      ptr(dev["phi_e"]), ptr(dev["w"]), float(st["t"])))
-        prob.step(1, rtol=args.rtol)
-        tt = C.c_double()
-        K._check(K._lib.knp_state_get(prob.handle, K.KNP_DEVICE, ptr(dev["c_i"]), ptr(dev["phi_i"]), ptr(dev["c_e"]),
-                                      ptr(dev["phi_e"]), ptr(dev["w"]), C.byref(tt)))
-        st["t"] = tt.value
-        for k in host:
-            host[k].copy_(dev[k], non_blocking=True)
+    for _ in range(steps):
+        K._check(K._lib.knp_state_set(prob.handle, K.KNP_HOST, ptr(host["c_i"]), ptr(host["phi_i"]),
+                                      ptr(host["c_e"]), ptr(host["phi_e"]), ptr(host["w"]), t.value))
+        prob.step(1, rtol=args.rtol, deflate=defl)
+        K._check(K._lib.knp_state_get(prob.handle, K.KNP_HOST, ptr(host["c_i"]), ptr(host["phi_i"]),
+                                      ptr(host["c_e"]), ptr(host["phi_e"]), ptr(host["w"]), ctypes.byref(t)))
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_ms = slowest_rank_ms(e2e_ms, world, "cuda")
-    e2e_value = job_value(n_dof, args.steps, world, e2e_ms)
-    return dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=h2d)
+    e2e_ms = slowest_rank_ms(e0.elapsed_time(e1), world, "cuda")
+    return dict(value=job_value(n_dof, steps, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=h2d, steps=steps,
+                path="knp_state_set(KNP_HOST) + knp_step + knp_state_get(KNP_HOST) from pinned host buffers")
 
 
-def mixed_run(cfg, mesh, torch, args, n_dof):
-    """The mixed-precision form (FP32 hierarchy and V-cycle under FP64 FGMRES), same workload."""
+def mixed_run(cfg, mesh, prob, torch, args, n_dof, window, steps, defl):
+    """The precision comparison on the window's first `steps` steps (setup excluded): the FP32
+    hierarchy at rtol 1e-8 (the mixed-precision form), the FP64 hierarchy at 1e-8 (the same
+    tolerance), and the plain FP64 path at 1e-10 (the tolerance of the FP64 configs); each
+    rate against the others. The timed problem is closed first to free its device memory."""
     import numpy as np
     from paper_2403_04491_gb300 import problem_from_config
-    mixed = None
-    if args.precision == "fp64":
-        out = {}
-        for rt in (1e-10, 1e-8):
+    out = {}
+    for key, pr_prec, rt in (("fp32_rtol_1e-08", 1, 1e-8), ("fp64_rtol_1e-08", 0, 1e-8), ("fp64_rtol_1e-10", 0, 1e-10)):
+        if pr_prec == (0 if args.precision == "fp64" else 1):
+            pm = prob
+        else:
             _, pm = problem_from_config(cfg, mesh=mesh)
-            pm.amg_setup(precision=1)
-            for _ in range(args.warmup):
-                pm.step(1, rtol=rt)
-            msm, itm, _, _ = measure(pm, torch, args.steps, rt)
-            out[f"rtol_{rt:g}"] = dict(value=n_dof * args.steps / (msm / 1e3), iters_per_step=float(np.mean(itm)))
+            pm.amg_setup(precision=pr_prec)
+        pm.state_set(window["c_i"], window["phi_i"], window["c_e"], window["phi_e"], window["w"], window["t"])
+        msm, itm, _, _ = measure(pm, torch, steps, rt, deflate=defl)
+        out[key] = dict(value=n_dof * steps / (msm / 1e3), iters_per_step=float(np.mean(itm)), iters=itm)
+        if pm is not prob:
             pm.close()
-        _, pf = problem_from_config(cfg, mesh=mesh)
-        pf.amg_setup(precision=0)
-        for _ in range(args.warmup):
-            pf.step(1, rtol=1e-8)
-        msf, itf, _, _ = measure(pf, torch, args.steps, 1e-8)
-        pf.close()
-        out["fp64_rtol_1e-08"] = dict(value=n_dof * args.steps / (msf / 1e3), iters_per_step=float(np.mean(itf)))
-        out["speedup_fp32_vs_fp64_at_rtol_1e-08"] = out["rtol_1e-08"]["value"] / out["fp64_rtol_1e-08"]["value"]
-        mixed = out
-    return mixed
+    out["steps"] = steps
+    out["speedup_fp32_vs_fp64_at_rtol_1e-08"] = out["fp32_rtol_1e-08"]["value"] / out["fp64_rtol_1e-08"]["value"]
+    out["speedup_fp32_rtol_1e-08_vs_plain_fp64_rtol_1e-10"] = (out["fp32_rtol_1e-08"]["value"]
+                                                               / out["fp64_rtol_1e-10"]["value"])
+    return out
 
 
-def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg,
-           workload=WORKLOAD, mem_gb=None):
+def report(args, work, world, rank, ms, iters, launches, prof, clocks, e2e, mixed, n_dof, t_create, t_amg, amg_rec,
+           workload, mem_gb, defl):
     import numpy as np
     import torch.distributed as dist
     value = job_value(n_dof, args.steps, world, ms)
@@ -434,11 +486,13 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
     import torch
     p64 = fp64_peak_tflops(torch)
     pf = json.load(open(PROFILE_FILE)) if os.path.exists(PROFILE_FILE) else {}
+    aux = prof[2]
+    ms_aux = ms * aux / args.steps   # the profiled passes cover the window's first `aux` steps
 
-    def roofline(prof_k, work, key, kind, name, fp64_bound):
+    def roofline(prof_k, work_k, key, kind, name, fp64_bound):
         """roofline object of one kernel from its per-launch event timing (n launches, total ms)."""
         n_launch, prof_ms = prof_k
-        bytes_per, flops_per = work
+        bytes_per, flops_per = work_k
         avg_s = prof_ms / n_launch / 1e3 if n_launch else None
         gbs = bytes_per / avg_s / 1e9 if avg_s else None
         ent = pf.get(key)
@@ -449,43 +503,40 @@ def report(args, prob, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
                    peak_source="measured" if "hbm_gbs" in peaks else "fallback")
         common = dict(kernel=name, traffic=traffic, algorithmic_bytes_per_launch=bytes_per,
                       algorithmic_flops_per_launch=flops_per, launches=n_launch,
-                      avg_launch_us=1e6 * avg_s if avg_s else None, share_of_step=prof_ms / ms if ms else None)
+                      avg_launch_us=1e6 * avg_s if avg_s else None,
+                      share_of_step=prof_ms / ms_aux if ms_aux else None)
         if fp64_bound:
-            # FP64 arithmetic bounds these kernels on GB300 (FP64 pipe 70-80% busy at about half
-            # of HBM, see profiles/): report against the measured FP64 rate, HBM fraction beside it
+            # FP64 arithmetic bounds these kernels on GB300 (its FP64 pipe is 1/64 of FP32): report
+            # against the measured FP64 rate, the HBM fraction beside it
             tf = flops_per / avg_s / 1e12 if avg_s else None
             return dict(bound="alu", achieved=tf, peak=p64, unit="TFLOP/s", frac=(tf / p64) if tf else None,
                         peak_source="measured FP64 DGEMM 4096^3 in this run", hbm=hbm, **common)
         return dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=hbm["frac"],
                     peak_source=hbm["peak_source"], **common)
 
-    # the dominant kernel: the operator SpMV (FP64 in both forms), the largest single kernel of
-    # the step (profiles/launches_bench_*); beside it the finest Chebyshev step of the V-cycle
-    roof = roofline(prof[1], spmv_work(prob), "spmv_fp64", "spmv",
-                    "k_op_apply (operator SpMV S^-1 A x, FP64)", True)
-    roof_vc = roofline(prof[0], dominant_kernel_work(prob, args.precision), f"cheb_fine_{args.precision}",
-                       "cheb_fine", "k_cheb_sell (finest-level Chebyshev step of the V-cycle)",
-                       args.precision == "fp64")
-    if mixed and args.precision == "fp64" and args.rtol == 1e-10:
-        # the mixed form at its tolerance (1e-8) against the plain FP64 path at its own (1e-10)
-        mixed["speedup_fp32_rtol_1e-08_vs_plain_fp64_rtol_1e-10"] = mixed["rtol_1e-08"]["value"] / value
+    # the dominant kernel: the operator SpMV (FP64 in both forms); beside it the finest Chebyshev
+    # step of the V-cycle
+    roof = roofline(prof[1], work["spmv"], "spmv_fp64", "spmv", "k_op_apply (operator SpMV S^-1 A x, FP64)", True)
+    roof_vc = roofline(prof[0], work["cheb"], f"cheb_fine_{args.precision}", "cheb_fine",
+                       "k_cheb_sell (finest-level Chebyshev step of the V-cycle)", args.precision == "fp64")
     cpu = None
-    if not args.no_baseline and world == 1 and args.config == 2:
-        # P2: the sample's mesh is halved, so that its node lattice (and DOF) is the P1 sample's
-        snx = SAMPLE_NX if args.degree == 1 else SAMPLE_NX // 2
-        r = run_oracle(3, 1, nx=snx, degree=args.degree)
-        v = r["n_dof"] * len(r["times"]) / sum(r["times"])
-        cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=oracle_sample_desc(snx, 3, args.degree))
+    if not args.no_baseline and world == 1:
+        cfg_id, nx = ORACLE_SAMPLE[args.config]
+        if args.degree == 2 and nx:
+            nx //= 2   # P2: the sample's mesh is halved, so that its node lattice is the P1 sample's
+        v, cores, sdof, _ = oracle_replicas(cfg_id, nx, 3, 1, degree=args.degree)
+        cpu = dict(value=v, unit=UNIT, cores=cores, kind="oracle",
+                   sample=oracle_sample_desc(cfg_id, nx, 3, 1, cores, sdof, args.degree))
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64" if args.precision == "fp64" else "f64 (FGMRES) / f32 (AMG)", data="synthetic",
                 config=dict(workload=workload, n_dof=n_dof, l2="working set per step > L2 (operator, hierarchy and "
                                                                "Krylov basis exceed 129 MB); no flush",
-                            precision=args.precision, rtol=args.rtol, restart=30,
+                            precision=args.precision, rtol=args.rtol, restart=30, deflate=defl,
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 iters_per_step=float(np.mean(iters)), iters=iters, setup_s=dict(create=t_create, amg=t_amg),
-                amg=prob.amg_info(), gpu_launches=launches, clocks=clocks, roofline=roof,
-                roofline_vcycle=roof_vc,
+                amg=work["amg"], amg_setup=amg_rec, gpu_launches=launches, clocks=clocks, roofline=roof,
+                roofline_vcycle=roof_vc, profiled_steps=aux,
                 device_memory_gb=mem_gb, host_peak_rss_gb=host_peak_rss_gb(),
                 e2e=e2e, cpu_baseline=cpu, mixed=mixed)
     print(json.dumps(line), flush=True)

@@ -261,7 +261,7 @@ typedef struct {
                           restart cycle began from (the first: x_0 = u_{n-1}) (the paper's
                           preconditioned test, Section 6.2, in the scaled norm, relative to the
                           iterate or, for a cold start, to the computed correction); with
-                          phi_e_group the phi_e part is floored at 1e-14 ||S phi|| */
+                          phi_e_group the phi_e part is floored at phi_e_floor ||S phi|| */
     int32_t restart;   /* 30 (Section 6.2) */
     int32_t max_it;    /* total iterations */
     int32_t phi_e_group;  /* 1: test the extracellular potentials as a third group (phi_e is some 1e-8
@@ -277,6 +277,8 @@ typedef struct {
                              the test of the paper's solver settings (Section 6.2),
                              ||M^-1 r||_2 <= rtol ||M^-1 f||_2 over the whole unscaled vector, for
                              comparing iteration counts with Tables 3 and 4 */
+    double phi_e_floor;   /* with phi_e_group: the phi_e part is tested against
+                             max(rtol ||S phi_e||, phi_e_floor ||S phi||); <= 0 selects 1e-14 */
 } knp_solve_opts;
 
 enum { KNP_TEST_SCALED = 0, KNP_TEST_PAPER = 1 };

@@ -517,7 +517,8 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
         if (NG == 3) {
             // phi_e is some 1e-8 of phi_i: below ~1e-14 of the whole potential the rounding of the
             // coupled equations sets the floor, and a tighter request would stagnate
-            tol[2] = std::max(tol[2], 1e-14 * std::sqrt(std::max(xn2[1] + xn2[2], 0.0)));
+            const double floor_rel = o.phi_e_floor > 0 ? o.phi_e_floor : 1e-14;
+            tol[2] = std::max(tol[2], floor_rel * std::sqrt(std::max(xn2[1] + xn2[2], 0.0)));
         }
     };
     if (paper_test) {
@@ -661,6 +662,13 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
             }
             // second pass skipped on the device (flag): the column is h1 and eta = |w'|
             const bool skipped = g.hh[2 * MAXV + MAXW] != 0.0;
+            if (monitor) {
+                // first Gram-Schmidt pass: |w'|^2 / |w|^2 = 1 - sum h1^2 / |w|^2
+                double h1 = 0.0;
+                for (int k = 0; k < nv; ++k) h1 += g.hh[k] * g.hh[k];
+                std::fprintf(stderr, "arnoldi j %d pass1 ratio %.3e second-pass skipped %d\n", j,
+                             g.hh[nv] > 0 ? 1.0 - h1 / g.hh[nv] : 0.0, (int)skipped);
+            }
             double s2 = g.hh[MAXV + nv];
             double eta2 = s2;
             for (int k = 0; k < nv; ++k) {

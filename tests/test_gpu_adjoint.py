@@ -123,3 +123,53 @@ def test_adjoint_rejects_kir_facets():
     prob.amg_setup()
     with pytest.raises(KnpError, match="Kir"):
         prob.adjoint_begin()
+
+
+@pytest.mark.slow
+def test_full_gradient_against_finite_differences():
+    """The differentiation workload at its full size (256^2 mesh, 16 cells, per-facet g_K, 200 steps
+    of 0.1 ms, checkpoints every 20, loss = sum over steps of phi_e^2 at 64 probes): the
+    checkpointed adjoint's directional derivatives match central differences of the GPU forward run
+    on 16 Gaussian directions (PCG64 seed 3): 8 in the per-facet g_K, 8 in the initial [K]_i.
+
+    The difference quotients use two step sizes combined to fourth order (Richardson), as the
+    oracle's own finite-difference pins do. Their accuracy is bounded by how well FP64 fixes phi_e:
+    phi_e is about 1e-6 of phi_i here, and perturbing the assembled operator's entries at 1e-16
+    moves the exact solution's phi_e by about 2.5e-7, so two correct FP64 runs agree on the loss to
+    about 1e-7 and a quotient to a few 1e-6. The bar is the oracle pins' 1e-5; a missing or
+    mis-signed adjoint term changes the derivatives by far more."""
+    import torch
+    from paper_2403_04491_gb300 import KNPFunction, Simulation, problem_from_config, probe_weights
+    cfg = make_config(4)
+    mesh, prob = problem_from_config(cfg)
+    prob.amg_setup()
+    m = cfg.mesh
+    ni, ne = mesh.nodes()
+    idx, w = probe_weights(m.coords, m.elems, m.elem_tag, ne, prob.N_i, prob.N_e, probe_points(cfg))
+    sim = Simulation(prob, idx, w, cfg.n_steps, checkpoint_every=20, rtol=1e-12)
+    g0 = torch.tensor(prob._facet_gleak[:, 1].copy())
+    c0 = torch.tensor(sim.s0["c_i"][1].copy())
+    gK, cK = g0.clone().requires_grad_(True), c0.clone().requires_grad_(True)
+    loss = (KNPFunction.apply(gK, cK, sim) ** 2).sum()
+    loss.backward()
+    grad_g, grad_c = gK.grad.numpy().copy(), cK.grad.numpy().copy()
+
+    def L(g, c):
+        with torch.no_grad():
+            return float((KNPFunction.apply(g, c, sim) ** 2).sum())
+
+    rng = np.random.Generator(np.random.PCG64(3))
+    for q in range(16):
+        if q < 8:
+            d, eps = 0.8 * rng.standard_normal(len(g0)), 0.2
+            Le = lambda e: L(g0 + e * torch.tensor(d), c0)
+            an = float(grad_g @ d)
+        else:
+            d, eps = 125.0 * rng.standard_normal(len(c0)), 0.01
+            Le = lambda e: L(g0, c0 + e * torch.tensor(d))
+            an = float(grad_c @ d)
+        d1 = Le(eps) - Le(-eps)
+        d2 = Le(eps / 2) - Le(-eps / 2)
+        fd = (8 * d2 - d1) / (6 * eps)
+        print(f"direction {q}: adjoint {an:.10e} finite differences {fd:.10e} rel {abs(fd - an) / abs(an):.2e}")
+        assert abs(fd - an) <= 1e-5 * abs(an), (q, an, fd)

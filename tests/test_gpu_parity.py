@@ -462,3 +462,38 @@ def test_deflation_cuts_iterations(name):
             assert ec <= TOL and ep <= TOL, (defl, n, ec, ep)
     print(name, "iterations without / with the coarse correction:", its[False], its[True])
     assert sum(its[True]) < sum(its[False])
+
+
+def _golden_64():
+    """The oracle's first three steps of the 64^3 HH workload (tests/golden/cfg2_64_states.npz, written
+    by tests/golden/make_cfg2_64_states.py from the oracle alone), reconstructed from the oracle's
+    initial state."""
+    import os
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "cfg2_64_states.npz"))
+    pb, s0 = oproblem.from_config(make_config(2))
+    states = []
+    for n in range(1, int(d["n_steps"]) + 1):
+        s = s0.copy()
+        for k in ("c_i", "phi_i", "c_e", "phi_e", "w"):
+            setattr(s, k, getattr(s0, k) + d[f"{k}_{n}"] * float(d[f"{k}_h"]))
+        states.append(s)
+    return pb, states
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64-amg", "fp32-amg"])
+def test_full_size_states_match_oracle(precision):
+    """The 64^3 HH workload at its full size (1,114,732 unknowns) in the bench's launch configuration
+    (FGMRES(30), rtol 1e-10, coarse correction on): the first three steps match the oracle's states
+    at 1e-8 relative l2 on the concentrations and on the potentials."""
+    from paper_2403_04491_gb300 import problem_from_config
+    pb, ref = _golden_64()
+    _, prob = problem_from_config(make_config(2))
+    assert prob.n_dof == 1114732
+    prob.amg_setup(precision=precision)
+    for n in range(1, len(ref) + 1):
+        prob.step(1, rtol=1e-10)
+        s = prob.state_get()
+        ec, ep = rel_errors(s, ref[n - 1])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep)
+        np.testing.assert_allclose(s["w"], ref[n - 1].w, rtol=1e-8, atol=1e-10)
