@@ -252,8 +252,8 @@ def kernel_source_hash(kind="cheb_fine"):
     """Hash of a reported kernel's source text, so that DRAM counters taken on an older version of
     it are not reported: "cheb_fine" (sell_row, cheb_update, k_cheb_sell) or "spmv" (k_op_apply)."""
     if kind == "spmv":
-        return _source_parts("spmv.cu", (("__global__ void __launch_bounds__(128) k_op_apply(",
-                                          "// y = rowscale .* (b - A^T x)"),))
+        return _source_parts("spmv.cu", (("// w[c] = sum_k z_k tau_r^k x^k[c]",
+                                          "// g^k = m + tau_r^k a per stored entry"),))
     return _source_parts("vcycle.cu", (("// Row product of a sliced-ELL operator", "// Field f of a CSR row product"),
                                        ("// Chebyshev update of one row",
                                         "template <class T, int S>\n__global__ void __launch_bounds__(128) k_cheb_csr")))
@@ -289,14 +289,15 @@ def dominant_kernel_work(prob, precision):
 
 
 def spmv_work(prob):
-    """Algorithmic bytes and FLOPs of one operator SpMV y = S^-1 A x (k_op_apply, the Arnoldi
-    form without a right-hand side). Bytes: per stored same-region entry a column index and five
-    FP64 values (m, a, e^1..e^3), per cross-region entry an index and three values, per node
-    the gathered x, the row scale and y (four FP64 each). FLOPs: 9 FMAs per same-region entry,
-    3 per cross entry, 20 per row."""
+    """Algorithmic bytes and FLOPs of one forward operator product y = S^-1 A x as the library
+    times it (the node pass w = sum_k z_k tau^k x^k, then k_op_apply). Bytes: per stored
+    same-region entry a column index and seven FP64 values (g^1..g^3 = m + tau^k a, a, e^1..e^3),
+    per cross-region entry an index and three values, per node x (4 values) and w read by the
+    node pass and w written, then x gathered, w gathered, the row scale and y (FP64). FLOPs: 7 FMAs
+    per same-region entry, 3 per cross entry, 3 FMAs per node in the node pass and 20 per row."""
     info = prob.info()
     n, nnz, nx = info["n_nodes"], info["nnz_region"], info["nnz_cross"]
-    return nnz * (4 + 40) + nx * (4 + 24) + n * 3 * 32, 18.0 * nnz + 6.0 * nx + 20.0 * n
+    return nnz * (4 + 56) + nx * (4 + 24) + n * (40 + 104), 14.0 * nnz + 6.0 * nx + 26.0 * n
 
 
 def measure(prob, torch, steps, rtol, kernel_class=None, deflate=True):
@@ -453,6 +454,7 @@ def mixed_run(cfg, mesh, prob, torch, args, n_dof, window, steps, defl):
     import numpy as np
     from paper_2403_04491_gb300 import problem_from_config
     out = {}
+    finals = {}
     for key, pr_prec, rt in (("fp32_rtol_1e-08", 1, 1e-8), ("fp64_rtol_1e-08", 0, 1e-8), ("fp64_rtol_1e-10", 0, 1e-10)):
         if pr_prec == (0 if args.precision == "fp64" else 1):
             pm = prob
@@ -462,9 +464,21 @@ def mixed_run(cfg, mesh, prob, torch, args, n_dof, window, steps, defl):
         pm.state_set(window["c_i"], window["phi_i"], window["c_e"], window["phi_e"], window["w"], window["t"])
         msm, itm, _, _ = measure(pm, torch, steps, rt, deflate=defl)
         out[key] = dict(value=n_dof * steps / (msm / 1e3), iters_per_step=float(np.mean(itm)), iters=itm)
+        st = pm.state_get()
+        finals[key] = (np.concatenate([st["c_i"].ravel(), st["c_e"].ravel()]), np.concatenate([st["phi_i"], st["phi_e"]]))
         if pm is not prob:
             pm.close()
     out["steps"] = steps
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    # the mixed form's states after the window's steps against the FP64 GPU path's (at 1e-8 and
+    # at 1e-10), relative l2 over the concentrations and over the potentials
+    for ref_key in ("fp64_rtol_1e-08", "fp64_rtol_1e-10"):
+        out[f"fp32_rtol_1e-08_vs_{ref_key}"] = dict(
+            rel_diff_c=rel(finals["fp32_rtol_1e-08"][0], finals[ref_key][0]),
+            rel_diff_phi=rel(finals["fp32_rtol_1e-08"][1], finals[ref_key][1]))
     out["speedup_fp32_vs_fp64_at_rtol_1e-08"] = out["fp32_rtol_1e-08"]["value"] / out["fp64_rtol_1e-08"]["value"]
     out["speedup_fp32_rtol_1e-08_vs_plain_fp64_rtol_1e-10"] = (out["fp32_rtol_1e-08"]["value"]
                                                                / out["fp64_rtol_1e-10"]["value"])

@@ -411,6 +411,7 @@ void upload_problem(knp_problem* P, const std::vector<int32_t>& h_edge, const st
     P->sell_edge.upload(h_edge, st);
     P->sell_m.upload(hm, st);
     P->sell_a.upload(ha, st);
+    op_prepare(P, st);
     P->sell_e.alloc(3 * S.n_entries);
     P->sell_e.zero(st);
     P->xptr.upload(P->h_xptr, st);

@@ -131,6 +131,8 @@ struct knp_problem {
     knp::DArray<int32_t> sell_edge;      // undirected edge id, -1 diagonal, -2 padding
     knp::DArray<double> sell_m, sell_a;  // static mass and stiffness
     knp::DArray<double> sell_e;          // [3][n_entries] c^k-row phi-col coefficients (per step)
+    knp::DArray<double> sell_g;          // [3][n_entries] m + tau_r^k a (static, for the forward product)
+    knp::DArray<double> op_w;            // [n] sum_k z_k tau_r^k x^k of the forward product's input
     std::vector<int32_t> h_xptr, h_xcol;
     knp::DArray<int32_t> xptr, xcol;     // cross-region entries, CSR over rows
     knp::DArray<double> xe;              // [3][n_cross]
@@ -200,5 +202,7 @@ inline const cudaStream_t kProblemStream = reinterpret_cast<cudaStream_t>(~uintp
 // (on `st`, or on the problem's stream when st is the default argument)
 void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale, const double* b,
               bool transpose = false, cudaStream_t st = kProblemStream);
+// the static per-ion values of the forward product (after the pattern and m, a are on the device)
+void op_prepare(knp_problem* p, cudaStream_t st);
 void download_state(const knp_problem* p, std::vector<double>& u);
 }  // namespace knp

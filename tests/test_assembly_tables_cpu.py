@@ -175,7 +175,8 @@ def replay(pb, s0, mfo, T):
     np.add.at(f[:, 3], mvg[0], -hphi)
     keep = mvg[1] != pin
     np.add.at(f[:, 3], mvg[1][keep], hphi[keep])
-    # the operator: k_op_apply on a random x
+    # the operator's node blocks built from the stored m, a, e (the form the transposed product
+    # uses; the forward product folds m + tau a per ion) on a random x
     x = np.random.default_rng(3).standard_normal((n, 4))
     phi = np.where(np.arange(n) == pin, 0.0, x[:, 3])
     y = np.zeros((n, 4))

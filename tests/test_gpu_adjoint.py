@@ -1,12 +1,14 @@
 """GPU adjoint against the oracle's adjoint (autograd of its torch residual form, exact LU
 solves): the transposed operator, and the gradients of L = sum_n sum_p phi_e(x_p, t_n)^2 with
-respect to the per-facet K leak conductance, u_0 and the HH gates w_0; and the
-torch.autograd.Function with checkpointing.
+respect to the per-facet K leak conductance, u_0 and the HH gates w_0; the torch.autograd.Function
+with checkpointing; and finite differences of the GPU forward loss on the full differentiation
+workload.
 
 Given the oracle's forward states, the GPU reverse sweep matches to relative l2 1e-6. From the
-GPU's own forward run the bar is 1e-5: the loss is built from phi_e, about 1e-8 of phi_i here,
-and the block-diagonal preconditioner's error estimate (the stopping test) sees phi_e's error
-only through its own block, so FGMRES at rtol 1e-12 leaves phi_e with relative errors near 1e-6.
+GPU's own forward run the bar is 1e-5. The loss is built from phi_e, about 1e-6 of phi_i on the
+16-cell workload, and FP64 fixes phi_e only loosely: perturbing the oracle's assembled entries by
+1e-16 moves its phi_e by 2.5e-7, and the GPU's phi_e differs from the oracle's by up to 2.8e-6 at
+any solver tolerance, phi_e floor or preconditioner, i.e. by the rounding of the two assemblies.
 """
 import numpy as np
 import pytest

@@ -119,16 +119,31 @@ def test_config2_horizon_past_the_stimulus(precision):
 
 @pytest.mark.slow
 def test_config3_subset_125_cells_mixed():
-    """The 125-cell workload at its 32^3 version (192,748 unknowns), FP32 hierarchy, 3 steps."""
+    """The 125-cell workload at its 32^3 version (192,748 unknowns) in its own configuration: FP32
+    hierarchy under FP64 FGMRES at rtol 1e-8, three steps. The error against the oracle is held to
+    10 rtol (measured: 4e-11 on the concentrations, 3.5e-8 on the potentials); the FP64 hierarchy
+    at the same rtol gives the same states to 1e-9 (the iterate's accuracy is set by the stopping
+    test, not by the precision of the preconditioner); and at rtol 1e-10 the FP32 form meets the
+    plain parity bar of 1e-8."""
     from paper_2403_04491_gb300 import problem_from_config
     cfg = make_config(3).with_nx(32)
     pb, ref = oracle_run(cfg, 3, "lu_p0")
-    _, prob = problem_from_config(cfg)
-    prob.amg_setup(precision=1)
-    for n in range(1, 4):
-        prob.step(1, rtol=1e-10)
-        ec, ep = rel_errors(prob.state_get(), ref[n])
-        assert ec <= TOL and ep <= TOL, (n, ec, ep)
+    runs = {}
+    for prec, rtol in ((1, 1e-8), (0, 1e-8), (1, 1e-10)):
+        _, prob = problem_from_config(cfg)
+        prob.amg_setup(precision=prec)
+        runs[prec, rtol] = []
+        for n in range(1, 4):
+            prob.step(1, rtol=rtol)
+            s = prob.state_get()
+            runs[prec, rtol].append(s)
+            ec, ep = rel_errors(s, ref[n])
+            bar = 10 * rtol if rtol > 1e-10 else TOL
+            print(f"fp{'32' if prec else '64'} rtol {rtol:g} step {n}: error c {ec:.2e} phi {ep:.2e}")
+            assert ec <= bar and ep <= bar, (prec, rtol, n, ec, ep)
+    for a, b in zip(runs[1, 1e-8], runs[0, 1e-8]):
+        for k in ("c_i", "phi_i", "c_e", "phi_e"):
+            assert np.linalg.norm(a[k] - b[k]) <= 1e-9 * np.linalg.norm(b[k]) + 1e-30, k
 
 
 def test_pin_on_a_membrane_vertex():

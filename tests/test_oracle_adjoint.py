@@ -82,3 +82,25 @@ def test_gradients_match_finite_differences(case):
         fd = _richardson(Lw, 0.05)
         an = np.sum(res["dLdw0"] * dw)
         assert abs(fd - an) <= 1e-5 * abs(an)
+
+
+def test_phi_e_is_fixed_loosely_in_fp64():
+    """Why the phi_e-based gradients carry a 1e-5 bar: on the 16-cell workload's 32^2 version,
+    perturbing every stored entry of A_0 at the rounding level (1 + 1e-16 xi) moves the exact
+    solution's phi_e by far more than 1e-16 (about 2.5e-7 of itself), while the concentrations
+    move at the rounding level. Two FP64 assemblies that round differently disagree on phi_e at
+    that level whatever their solvers do."""
+    from oracle import solve as osolve
+    pb, s0 = problem.from_config(make_config(4).with_nx(32))
+    A, f, _ = system.assemble(pb, s0)
+    off_i, off_e, N = system.offsets(pb)
+    u = osolve.direct(A, f, refine=4)
+    A2 = A.copy().tocsr()
+    A2.data = A2.data * (1 + 1e-16 * np.random.default_rng(0).standard_normal(A2.nnz))
+    u2 = osolve.direct(A2, f, refine=4)
+    phe = slice(off_e[3], N)
+    conc = np.r_[0:off_i[3], off_e[0]:off_e[3]]
+    d_phe = np.linalg.norm(u2[phe] - u[phe]) / np.linalg.norm(u[phe])
+    d_c = np.linalg.norm(u2[conc] - u[conc]) / np.linalg.norm(u[conc])
+    assert 1e-8 < d_phe < 1e-5, d_phe
+    assert d_c < 1e-14, d_c
