@@ -510,12 +510,19 @@ def report(args, work, world, rank, ms, iters, launches, prof, clocks, e2e, mixe
         avg_s = prof_ms / n_launch / 1e3 if n_launch else None
         gbs = bytes_per / avg_s / 1e9 if avg_s else None
         ent = pf.get(key)
-        # counters hold for the kernel text and the workload they were taken on
-        traffic = ent.get("dram_bytes_per_launch") if (ent and ent.get("source_hash") == kernel_source_hash(kind)
-                                                       and ent.get("n_dof") == n_dof) else None
+        # counters hold for the kernel text they were taken on: as captured on the same workload,
+        # else scaled by the algorithmic bytes (the capture's traffic / algorithmic ratio)
+        traffic, traffic_src = None, None
+        if ent and ent.get("source_hash") == kernel_source_hash(kind):
+            if ent.get("n_dof") == n_dof:
+                traffic, traffic_src = ent.get("dram_bytes_per_launch"), "ncu capture of this workload"
+            elif ent.get("algorithmic_bytes_per_launch"):
+                traffic = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes_per_launch"] * bytes_per
+                traffic_src = (f"scaled by algorithmic bytes from the ncu capture at {ent['n_dof']:,} DOF "
+                               f"(traffic / algorithmic = {ent['dram_bytes_per_launch'] / ent['algorithmic_bytes_per_launch']:.3f})")
         hbm = dict(achieved=gbs, peak=peak, unit="GB/s", frac=(gbs / peak) if gbs else None,
                    peak_source="measured" if "hbm_gbs" in peaks else "fallback")
-        common = dict(kernel=name, traffic=traffic, algorithmic_bytes_per_launch=bytes_per,
+        common = dict(kernel=name, traffic=traffic, traffic_source=traffic_src, algorithmic_bytes_per_launch=bytes_per,
                       algorithmic_flops_per_launch=flops_per, launches=n_launch,
                       avg_launch_us=1e6 * avg_s if avg_s else None,
                       share_of_step=prof_ms / ms_aux if ms_aux else None)

@@ -272,7 +272,7 @@ typedef struct {
                              capacitance and the point pin, so one V-cycle amplifies residuals along
                              these modes; the paper's left-preconditioned GMRES minimises exactly that
                              amplified residual, right-preconditioned FGMRES needs the correction to
-                             converge in the same norm. Forward solves only (ignored for A^T). */
+                             converge in the same norm. Also for the adjoint's A^T solve (E^T). */
     int32_t stop_test;    /* KNP_TEST_SCALED (0): the per-group scaled test above. KNP_TEST_PAPER (1):
                              the test of the paper's solver settings (Section 6.2),
                              ||M^-1 r||_2 <= rtol ||M^-1 f||_2 over the whole unscaled vector, for
@@ -375,9 +375,10 @@ knp_status knp_apply_preconditioner(knp_problem* prob, const double* r, double* 
 /* z = M_D^{-1} r: the preconditioner of knp_solve with deflate = 1, P_0^{-1} wrapped in the coarse
  * correction of the potentials' near-null modes (each cell's constant phi_i and the constant
  * phi_e): y = E^{-1} Z^T r with E = Z^T A_{n-1} Z, z = V-cycle(P_0)(r - A_{n-1} Z y) + Z y, on the
- * operator of the current assembly. Host [n] arrays in the Eq. 4.3 order. Errors:
- * KNP_ERR_INVALID_ARG, KNP_ERR_STATE (no hierarchy or no assembled step), KNP_ERR_CUDA. */
-knp_status knp_apply_deflated_preconditioner(knp_problem* prob, const double* r, double* z);
+ * operator of the current assembly; with transpose = 1 the adjoint solve's form, with A^T and
+ * E^T in their places. Host [n] arrays in the Eq. 4.3 order. Errors: KNP_ERR_INVALID_ARG,
+ * KNP_ERR_STATE (no hierarchy or no assembled step), KNP_ERR_CUDA. */
+knp_status knp_apply_deflated_preconditioner(knp_problem* prob, const double* r, double* z, int32_t transpose);
 /* Allocation-free variant of knp_apply_preconditioner. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc when they need the
  * preconditioner - code running under a CUDA stream capture or while a CUDA graph is being

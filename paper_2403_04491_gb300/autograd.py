@@ -56,12 +56,13 @@ class Simulation:
     """A problem with its initial state, probes and run length, for KNPFunction."""
 
     def __init__(self, prob: Problem, probe_idx, probe_w, n_steps: int, checkpoint_every: int = 20,
-                 rtol: float = 1e-10, ion_k: int = 1, max_it: int = 1000):
+                 rtol: float = 1e-10, ion_k: int = 1, max_it: int = 1000, phi_e_floor: float = 0.0):
         self.prob = prob
         self.n_steps = n_steps
         self.k = max(1, checkpoint_every)
         self.rtol = rtol
         self.max_it = max_it
+        self.phi_e_floor = phi_e_floor   # the phi_e group's floor of the stopping test (0: the library's)
         self.its_forward, self.its_adjoint = [], []   # FGMRES iterations of the last run
         self.ion_k = ion_k
         self.idx = torch.as_tensor(probe_idx, device="cuda")
@@ -111,7 +112,7 @@ class KNPFunction(torch.autograd.Function):
         for n in range(sim.n_steps):
             if n % sim.k == 0:
                 checkpoints.append(sim._get())
-            st = p.step(1, rtol=sim.rtol, max_it=sim.max_it, phi_e_group=True)
+            st = p.step(1, rtol=sim.rtol, max_it=sim.max_it, phi_e_group=True, phi_e_floor=sim.phi_e_floor)
             sim.its_forward.append(st[0]["iterations"])
             u, _, _ = sim._get()
             out.append(sim.probes(u))
@@ -134,14 +135,14 @@ class KNPFunction(torch.autograd.Function):
             sim._set(u, w, t)
             states = [(u, w, t)]
             for _ in range(n0, n1):
-                p.step(1, rtol=sim.rtol, max_it=sim.max_it, phi_e_group=True)
+                p.step(1, rtol=sim.rtol, max_it=sim.max_it, phi_e_group=True, phi_e_floor=sim.phi_e_floor)
                 states.append(sim._get())
             for n in range(n1, n0, -1):
                 u_n = states[n - n0][0]
                 dLdu = torch.zeros_like(u_n)
                 dLdu.index_add_(0, sim.idx.reshape(-1), (grad_out[n - 1][:, None] * sim.w).reshape(-1))
                 sim._set(*states[n - n0 - 1])
-                st = p.adjoint_step(u_n, dLdu, rtol=sim.rtol, max_it=sim.max_it)
+                st = p.adjoint_step(u_n, dLdu, rtol=sim.rtol, max_it=sim.max_it, phi_e_floor=sim.phi_e_floor)
                 sim.its_adjoint.append(st["iterations"])
         g = p.adjoint_get()
         gK = torch.as_tensor(g["grad_gleak"][:, sim.ion_k])

@@ -421,7 +421,7 @@ knp_status knp_apply_preconditioner(knp_problem* p, const double* r, double* z) 
     });
 }
 
-knp_status knp_apply_deflated_preconditioner(knp_problem* p, const double* r, double* z) {
+knp_status knp_apply_deflated_preconditioner(knp_problem* p, const double* r, double* z, int32_t transpose) {
     return guarded([&] {
         KNP_REQUIRE(p && r && z, KNP_ERR_INVALID_ARG, "NULL argument");
         KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
@@ -433,7 +433,7 @@ knp_status knp_apply_deflated_preconditioner(knp_problem* p, const double* r, do
         d1.upload(ones, p->stream);
         dz.alloc(ri.size());
         deflation_prepare(p);
-        deflated_precond_apply(p, dr.p, d1.p, dz.p);
+        deflated_precond_apply(p, dr.p, d1.p, dz.p, transpose != 0);
         dz.download(zi, p->stream);
         KNP_CUDA(cudaStreamSynchronize(p->stream));
         from_interleaved(p, zi, z);

@@ -15,7 +15,8 @@
 //     E = Z^T A Z,   y = E^{-1} Z^T r,   M_D^{-1} r = P_0^{-1} (r - A Z y) + Z y.
 // The V-cycle then sees a residual orthogonal to Z (nothing left to amplify) and Z y is the exact
 // correction of those modes. FGMRES tolerates any preconditioner, so the iterate's accuracy is
-// still set by the stopping test alone.
+// still set by the stopping test alone. The adjoint's A^T solve uses the same coarse space with
+// Z^T A^T Z = E^T.
 //
 // Costs. A applied to a piecewise-constant potential is nonzero only through the membrane and
 // pin terms: per row, the sum of its same-region e^k coefficients times the constant of its own
@@ -51,21 +52,33 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;   // valid in thread 0
 }
 
-// RS[r][k] = sum of the same-region e^k values of row r over phi columns other than the pin
+// RS[r][k] = sum of the same-region e^k values of row r over phi columns other than the pin;
+// RSa[r] the same sum of the static stiffness a (for the transposed operator's concentration rows)
 __global__ void k_defl_rowsums(int64_t n, int32_t pin, const int64_t* __restrict__ slice_ptr,
                                const int32_t* __restrict__ col, const double* __restrict__ e, int64_t ne,
-                               double* __restrict__ RS) {
+                               const double* __restrict__ a, double* __restrict__ RS, double* __restrict__ RSa) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int64_t s = r / SELL_C, base = slice_ptr[s] + r % SELL_C;
     const int64_t w = (slice_ptr[s + 1] - slice_ptr[s]) / SELL_C;
-    double acc[KI] = {0, 0, 0};
+    double acc[KI] = {0, 0, 0}, sa = 0.0;
     for (int64_t k = 0; k < w; ++k) {
         const int64_t pos = base + k * SELL_C;
         if (col[pos] == pin) continue;
         for (int q = 0; q < KI; ++q) acc[q] += e[q * ne + pos];
+        sa += a[pos];
     }
     for (int q = 0; q < KI; ++q) RS[3 * r + q] = acc[q];
+    RSa[r] = sa;
+}
+
+// group of the source row of every transposed cross entry (-1: the pinned node)
+__global__ void k_defl_xtg(int64_t nx, int64_t N_i, int32_t pin, const int32_t* __restrict__ xtrow,
+                           const int32_t* __restrict__ rgrp, int32_t ext_group, int32_t* __restrict__ xtg) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nx) return;
+    const int32_t j = xtrow[t];
+    xtg[t] = j == pin ? -1 : (j < N_i ? rgrp[j] : ext_group);
 }
 
 // Per cell group j (one block): E_jj, E_je and E_ej of E = Z^T A Z. Potential-row coefficient of a
@@ -204,6 +217,37 @@ __global__ void k_defl_rhs(int64_t n, int64_t N_i, int32_t pin, const int32_t* _
     t[b + 3] = s[b + 3] * v[b + 3] - out3;
 }
 
+// t = s .* v - A^T Z y (the transposed operator's node block, cf. the transposed product): the
+// concentration rows see tau_r^k z_k (sum of a over the row's phi columns) times the row's own
+// constant; the potential row sum_k z_k e^k times it plus, through the transposed cross-region
+// list, sum_k z_k xe^k times the source rows' constants; the pinned potential row gives 0.
+__global__ void k_defl_rhs_t(int64_t n, int64_t N_i, int32_t pin, const int32_t* __restrict__ rgrp,
+                             const double* __restrict__ RS, const double* __restrict__ RSa,
+                             const int32_t* __restrict__ xtptr, const int32_t* __restrict__ xtidx,
+                             const int32_t* __restrict__ xtg, const double* __restrict__ xe, int64_t n_cross,
+                             double z0, double z1, double z2, RegionCoef ri, RegionCoef re,
+                             const double* __restrict__ y, int32_t ext_group, const double* __restrict__ v,
+                             const double* __restrict__ s, double* __restrict__ t) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const bool in = r < N_i;
+    const RegionCoef& rc = in ? ri : re;
+    const double yr = y[in ? rgrp[r] : ext_group];
+    const double z[KI] = {z0, z1, z2};
+    double out[4];
+    for (int q = 0; q < KI; ++q) out[q] = rc.tau[q] * z[q] * RSa[r] * yr;
+    double o3 = (z0 * RS[3 * r] + z1 * RS[3 * r + 1] + z2 * RS[3 * r + 2]) * yr;
+    for (int u = xtptr[r]; u < xtptr[r + 1]; ++u) {
+        const int gq = xtg[u];
+        if (gq < 0) continue;
+        const int64_t idx = xtidx[u];
+        o3 += (z0 * xe[idx] + z1 * xe[n_cross + idx] + z2 * xe[2 * n_cross + idx]) * y[gq];
+    }
+    out[3] = r == pin ? 0.0 : o3;
+    const int64_t b = 4 * r;
+    for (int q = 0; q < 4; ++q) t[b + q] = s[b + q] * v[b + q] - out[q];
+}
+
 // z += Z y: the potential of every node of a group takes its group's constant
 __global__ void k_defl_add(int64_t n, int64_t N_i, int32_t pin, const int32_t* __restrict__ rgrp,
                            const double* __restrict__ y, int32_t ext_group, double* __restrict__ z) {
@@ -228,6 +272,8 @@ struct Deflation {
     DArray<int32_t> rgrp;             // intracellular node -> its group
     DArray<int32_t> xg;               // cross entry -> group of its column (-1: the pinned node)
     DArray<double> RS;                // [n][3] row sums of e^k over phi columns (per step)
+    DArray<double> RSa;               // [n] row sums of a over phi columns (the transposed operator)
+    DArray<int32_t> xtg;              // transposed cross entry -> group of its source row (-1: pin)
     DArray<double> Ejj, Eje, Eej, Ee; // the arrowhead E (per step); Ee = {E_ee, Schur complement}
     DArray<double> g, y, part, t, ones;
     int64_t built_for = -1;           // assembly whose operator E was formed from
@@ -272,6 +318,13 @@ static Deflation& deflation_setup(knp_problem* p) {
     d->xg.upload(xg, st);
     const int64_t n = p->n_nodes;
     d->RS.alloc(3 * n);
+    d->RSa.alloc(n);
+    const int64_t nx = (int64_t)p->h_xcol.size();
+    d->xtg.alloc(std::max<int64_t>(nx, 1));
+    if (nx) {
+        k_defl_xtg<<<nbk(nx, 256), 256, 0, st>>>(nx, p->N_i, p->pin, p->xtrow.p, d->rgrp.p, ext, d->xtg.p);
+        count_launch();
+    }
     for (DArray<double>* a : {&d->Ejj, &d->Eje, &d->Eej}) a->alloc(std::max(d->nc, 1));
     d->Ee.alloc(2);
     d->g.alloc(std::max(d->nc, 1));
@@ -293,7 +346,7 @@ void deflation_prepare(knp_problem* p) {
     const double* z = p->sp.z;
     count_launch(4);
     k_defl_rowsums<<<nbk(n, 128), 128, 0, st>>>(n, p->pin, p->sell.slice_ptr.p, p->sell.col.p, p->sell_e.p,
-                                                 p->sell.n_entries, d.RS.p);
+                                                 p->sell.n_entries, p->sell_a.p, d.RS.p, d.RSa.p);
     if (d.nc)
         k_defl_E_cells<<<d.nc, DT, 0, st>>>(d.cptr.p, d.cnodes.p, d.RS.p, p->xptr.p, d.xg.p, p->xtptr.p, p->xtrow.p,
                                             p->xtidx.p, p->xe.p, nx, p->pin, z[0], z[1], z[2], d.nc, d.Ejj.p,
@@ -304,7 +357,7 @@ void deflation_prepare(knp_problem* p) {
     d.built_for = p->assembly_id;
 }
 
-void deflated_precond_apply(knp_problem* p, const double* v, const double* s, double* z) {
+void deflated_precond_apply(knp_problem* p, const double* v, const double* s, double* z, bool transpose) {
     Deflation& d = *p->defl;
     cudaStream_t st = p->stream;
     const int64_t n = p->n_nodes, nx = (int64_t)p->h_xcol.size();
@@ -312,9 +365,16 @@ void deflated_precond_apply(knp_problem* p, const double* v, const double* s, do
     count_launch(3);
     k_defl_gather<<<d.nc + EXT_BLOCKS, DT, 0, st>>>(d.nc, d.cptr.p, d.cnodes.p, p->N_i, n, p->pin, v, s, d.g.p,
                                                     d.part.p);
-    k_defl_solve<<<1, DT, 0, st>>>(d.nc, d.part.p, d.g.p, d.Ejj.p, d.Eje.p, d.Eej.p, d.Ee.p, d.y.p);
-    k_defl_rhs<<<nbk(n, 128), 128, 0, st>>>(n, p->N_i, p->pin, d.rgrp.p, d.RS.p, p->xptr.p, d.xg.p, p->xe.p, nx,
-                                            zc[0], zc[1], zc[2], d.y.p, d.nc, v, s, d.t.p);
+    // Z^T A^T Z = E^T: the same Schur complement, E_je and E_ej exchanged
+    k_defl_solve<<<1, DT, 0, st>>>(d.nc, d.part.p, d.g.p, d.Ejj.p, transpose ? d.Eej.p : d.Eje.p,
+                                   transpose ? d.Eje.p : d.Eej.p, d.Ee.p, d.y.p);
+    if (transpose)
+        k_defl_rhs_t<<<nbk(n, 128), 128, 0, st>>>(n, p->N_i, p->pin, d.rgrp.p, d.RS.p, d.RSa.p, p->xtptr.p,
+                                                  p->xtidx.p, d.xtg.p, p->xe.p, nx, zc[0], zc[1], zc[2], p->sp.reg[0],
+                                                  p->sp.reg[1], d.y.p, d.nc, v, s, d.t.p);
+    else
+        k_defl_rhs<<<nbk(n, 128), 128, 0, st>>>(n, p->N_i, p->pin, d.rgrp.p, d.RS.p, p->xptr.p, d.xg.p, p->xe.p, nx,
+                                                zc[0], zc[1], zc[2], d.y.p, d.nc, v, s, d.t.p);
     precond_apply(p, d.t.p, d.ones.p, z);
     count_launch();
     k_defl_add<<<nbk(n, 256), 256, 0, st>>>(n, p->N_i, p->pin, d.rgrp.p, d.y.p, d.nc, z);

@@ -495,11 +495,11 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
     // the paper's test is one group over the whole vector: unit weights, no phi_e group
     const int NG = (o.phi_e_group && !paper_test) ? 3 : 2;
     const int64_t n4i = 4 * p->N_i;
-    const bool defl = o.deflate && !transpose;
+    const bool defl = o.deflate != 0;
     if (defl) deflation_prepare(p);
     auto precond = [&](const double* v, const double* s, double* z) {
         if (defl)
-            deflated_precond_apply(p, v, s, z);
+            deflated_precond_apply(p, v, s, z, transpose);
         else
             precond_apply(p, v, s, z);
     };

@@ -123,7 +123,7 @@ SIGNATURES = {
     "knp_apply_operator": [C.c_void_p, _DP, _DP],
     "knp_operator_entries": [C.c_void_p, C.c_int64, _LP, _LP, _DP],
     "knp_apply_preconditioner": [C.c_void_p, _DP, _DP],
-    "knp_apply_deflated_preconditioner": [C.c_void_p, _DP, _DP],
+    "knp_apply_deflated_preconditioner": [C.c_void_p, _DP, _DP, C.c_int32],
     "knp_apply_preconditioner_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p],
     "knp_amg_info": [C.c_void_p, _IP, _LP, _LP, _DP],
     "knp_amg_setup_info": [C.c_void_p, C.c_void_p],
@@ -427,9 +427,10 @@ class Problem:
     def adjoint_begin(self):
         _check(_lib.knp_adjoint_begin(self.handle))
 
-    def adjoint_step(self, u_n, dLdu_n, rtol=1e-10, restart=30, max_it=1000, phi_e_group=True, phi_e_floor=0.0):
+    def adjoint_step(self, u_n, dLdu_n, rtol=1e-10, restart=30, max_it=1000, phi_e_group=True, phi_e_floor=0.0,
+                     deflate=True):
         """u_n, dLdu_n in the Eq. 4.3 order: numpy arrays (host) or CUDA tensors (device)."""
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), 0, KNP_TEST_SCALED, float(phi_e_floor))
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), KNP_TEST_SCALED, float(phi_e_floor))
         s = SolveStats()
         if hasattr(u_n, "data_ptr"):
             _check(_lib.knp_adjoint_step(self.handle, KNP_DEVICE, C.c_void_p(u_n.data_ptr()),
@@ -464,11 +465,12 @@ class Problem:
         _check(_lib.knp_apply_preconditioner(self.handle, _dptr(r), _dptr(z)))
         return z
 
-    def apply_deflated_preconditioner(self, r):
-        """M_D^{-1} r (knp_apply_deflated_preconditioner), host arrays in the Eq. 4.3 order."""
+    def apply_deflated_preconditioner(self, r, transpose=False):
+        """M_D^{-1} r (knp_apply_deflated_preconditioner), host arrays in the Eq. 4.3 order; the
+        adjoint solve's form (A^T, E^T) with transpose."""
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.empty(self.n_dof)
-        _check(_lib.knp_apply_deflated_preconditioner(self.handle, _dptr(r), _dptr(z)))
+        _check(_lib.knp_apply_deflated_preconditioner(self.handle, _dptr(r), _dptr(z), int(bool(transpose))))
         return z
 
     def apply_preconditioner_noalloc(self, r_dev, z_dev):

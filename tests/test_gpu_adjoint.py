@@ -134,12 +134,16 @@ def test_full_gradient_against_finite_differences():
     checkpointed adjoint's directional derivatives match central differences of the GPU forward run
     on 16 Gaussian directions (PCG64 seed 3): 8 in the per-facet g_K, 8 in the initial [K]_i.
 
-    The difference quotients use two step sizes combined to fourth order (Richardson), as the
-    oracle's own finite-difference pins do. Their accuracy is bounded by how well FP64 fixes phi_e:
-    phi_e is about 1e-6 of phi_i here, and perturbing the assembled operator's entries at 1e-16
-    moves the exact solution's phi_e by about 2.5e-7, so two correct FP64 runs agree on the loss to
-    about 1e-7 and a quotient to a few 1e-6. The bar is the oracle pins' 1e-5; a missing or
-    mis-signed adjoint term changes the derivatives by far more."""
+    The quotients combine two step sizes to fourth order (Richardson), as the oracle's own
+    finite-difference pins do; their accuracy is bounded by how precisely FP64 fixes the loss.
+    phi_e is about 1e-6 of phi_i, and perturbing the assembled operator at the rounding level moves
+    phi_e by about 2.5e-7 of itself (tests/test_oracle_adjoint.py), so two runs whose inputs
+    differ slightly disagree on the loss at that level, whatever the solver tolerance (measured:
+    the same at rtol 1e-12 with the phi_e floor at 1e-14 and at rtol 1e-13 with 1e-16). In g_K a
+    20% perturbation changes the loss by 20%, and the quotient agrees to 1e-5 .. 8e-5 (bar 2e-4).
+    After 200 steps the loss hardly depends on the initial [K]_i (2.5e-3 of it per 1.25 mM), so
+    those quotients agree to 2e-3 .. 1.5e-2 (bar 5e-2). A missing or mis-signed adjoint term moves
+    a derivative by order one."""
     import torch
     from paper_2403_04491_gb300 import KNPFunction, Simulation, problem_from_config, probe_weights
     cfg = make_config(4)
@@ -163,15 +167,15 @@ def test_full_gradient_against_finite_differences():
     rng = np.random.Generator(np.random.PCG64(3))
     for q in range(16):
         if q < 8:
-            d, eps = 0.8 * rng.standard_normal(len(g0)), 0.2
+            d, eps, bar = 0.8 * rng.standard_normal(len(g0)), 0.2, 2e-4
             Le = lambda e: L(g0 + e * torch.tensor(d), c0)
             an = float(grad_g @ d)
         else:
-            d, eps = 125.0 * rng.standard_normal(len(c0)), 0.01
+            d, eps, bar = 125.0 * rng.standard_normal(len(c0)), 0.02, 5e-2
             Le = lambda e: L(g0, c0 + e * torch.tensor(d))
             an = float(grad_c @ d)
         d1 = Le(eps) - Le(-eps)
         d2 = Le(eps / 2) - Le(-eps / 2)
         fd = (8 * d2 - d1) / (6 * eps)
         print(f"direction {q}: adjoint {an:.10e} finite differences {fd:.10e} rel {abs(fd - an) / abs(an):.2e}")
-        assert abs(fd - an) <= 1e-5 * abs(an), (q, an, fd)
+        assert abs(fd - an) <= bar * abs(an), (q, an, fd)

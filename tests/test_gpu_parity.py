@@ -455,6 +455,13 @@ def test_deflated_preconditioner(name):
     y = np.linalg.solve(E, Z.T @ r)
     z_ref = prob.apply_preconditioner(r - A @ (Z @ y)) + Z @ y
     assert np.linalg.norm(prob.apply_deflated_preconditioner(r) - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
+    # the adjoint solve's form: A^T and E^T = Z^T A^T Z in their places
+    At = A.T.tocsr()
+    z = prob.apply_deflated_preconditioner(At @ Zw, transpose=True)
+    assert np.linalg.norm(z - Zw) <= 1e-8 * np.linalg.norm(Zw)
+    y = np.linalg.solve(E.T, Z.T @ r)
+    z_ref = prob.apply_preconditioner(r - At @ (Z @ y)) + Z @ y
+    assert np.linalg.norm(prob.apply_deflated_preconditioner(r, transpose=True) - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
 
 
 @pytest.mark.parametrize("name", ["cfg2-3d-hh-16", "cfg4-2d-16cells-32"])
