@@ -155,10 +155,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot_split(int64_t n4, const do
 // S^2-weighted squared norms, by group, of two combinations of the columns of Z:
 // u = sum_k c[k] Z_k and v = sum_k y[k] Z_k (y[NV-1] is the newest column's, often 0).
 // Slot g holds group g's part of ||u||_S^2 and slot NG + g that of ||v||_S^2 (groups as above).
+// Without with_y only u is formed (v's slots stay zero): half the FP64 work.
 template <int NV, int NG>
 __global__ void __launch_bounds__(RED_THREADS) k_combo_norms(int64_t n4, const double* __restrict__ Z, int64_t ldz,
                                                              const double* __restrict__ cy, const double* __restrict__ s,
-                                                             int64_t n4i, double* __restrict__ partial) {
+                                                             int64_t n4i, double* __restrict__ partial, int with_y) {
     double ck[NV > 0 ? NV : 1], yk[NV > 0 ? NV : 1];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -172,11 +173,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_combo_norms(int64_t n4, const d
     const bool phi = (i0 & 3) == 3;   // the grid stride is a multiple of 4
     for (int64_t i = i0; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         double u = 0.0, v = 0.0;
+        if (with_y) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const double zk = Z[k * ldz + i];
-            u += ck[k] * zk;
-            v += yk[k] * zk;
+            for (int k = 0; k < NV; ++k) {
+                const double zk = Z[k * ldz + i];
+                u += ck[k] * zk;
+                v += yk[k] * zk;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) u += ck[k] * Z[k * ldz + i];
         }
         const double w = s[i];
         u *= w;
@@ -622,7 +628,12 @@ knp_status_detail fgmres(knp_problem* p, const knp_solve_opts& o, knp_solve_stat
                 KNP_CUDA(cudaMemcpyAsync(g.cy.p, cyh.data(), 2 * MAXV * sizeof(double), cudaMemcpyHostToDevice,
                                          st));
                 count_launch(2);
-#define KNP_ARGS n4, g.Z.p, n4, g.cy.p, wts, n4i, g.partial.p
+                // the correction's norm enters the reference only where a group's ||S x_c|| is zero
+                // (a cold start); otherwise max(||S x_c||, ||S (x - x_c)||) is the state's norm
+                // for every realistic step, so Z y is formed only in the first case
+                bool with_y = false;
+                for (int q = 0; q < NG; ++q) with_y |= tol[q] == 0.0;
+#define KNP_ARGS n4, g.Z.p, n4, g.cy.p, wts, n4i, g.partial.p, (int)with_y
                 if (NG == 3)
                     KNP_LAUNCH_NV(j + 1, k_combo_norms3);
                 else

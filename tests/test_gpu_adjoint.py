@@ -139,8 +139,10 @@ def test_full_gradient_against_finite_differences():
     phi_e is about 1e-6 of phi_i, and perturbing the assembled operator at the rounding level moves
     phi_e by about 2.5e-7 of itself (tests/test_oracle_adjoint.py), so two runs whose inputs
     differ slightly disagree on the loss at that level, whatever the solver tolerance (measured:
-    the same at rtol 1e-12 with the phi_e floor at 1e-14 and at rtol 1e-13 with 1e-16). In g_K a
-    20% perturbation changes the loss by 20%, and the quotient agrees to 1e-5 .. 8e-5 (bar 2e-4).
+    the same at rtol 1e-12 with the phi_e floor at 1e-14 and at rtol 1e-13 with 1e-16): on this
+    200-step run the loss carries about 1e-5 relative noise, and the same direction's quotient
+    moved between 1e-5 and 8e-5 with the solver settings alone. A 20% perturbation of g_K changes
+    the loss by 5-20% along these directions, and the quotients agree to 1e-5 .. 5e-4 (bar 2e-3).
     After 200 steps the loss hardly depends on the initial [K]_i (2.5e-3 of it per 1.25 mM), so
     those quotients agree to 2e-3 .. 1.5e-2 (bar 5e-2). A missing or mis-signed adjoint term moves
     a derivative by order one."""
@@ -167,7 +169,7 @@ def test_full_gradient_against_finite_differences():
     rng = np.random.Generator(np.random.PCG64(3))
     for q in range(16):
         if q < 8:
-            d, eps, bar = 0.8 * rng.standard_normal(len(g0)), 0.2, 2e-4
+            d, eps, bar = 0.8 * rng.standard_normal(len(g0)), 0.2, 2e-3
             Le = lambda e: L(g0 + e * torch.tensor(d), c0)
             an = float(grad_g @ d)
         else:
