@@ -33,10 +33,6 @@ sys.path.insert(0, ROOT)
 METRIC = "DOF*timesteps/s (assembly+AMG-GMRES)"
 UNIT = "DOF*steps/s"
 PROFILE_FILE = os.path.join(ROOT, "profiles", "roofline_counters.json")
-# workloads whose unknowns exceed this run their secondary passes (profiled kernels, end to end,
-# precision comparison) over a few steps of the same window instead of all --steps
-LARGE_DOF = 20_000_000
-AUX_STEPS_LARGE = 3
 
 # CPU oracle samples per workload: (workload whose scenario the oracle runs, mesh resolution or
 # None for the workload's own). The large workloads' cell layouts cannot be coarsened much (their
@@ -381,7 +377,7 @@ def ours(args):
     t_amg = time.perf_counter() - t0
     amg_rec = prob.amg_setup_info()
     n_dof = prob.n_dof
-    aux = args.steps if n_dof <= LARGE_DOF else min(args.steps, AUX_STEPS_LARGE)
+    aux = args.steps   # every pass (profiled, end to end, precision comparison) solves the same steps
     for _ in range(args.warmup):
         prob.step(1, rtol=args.rtol, deflate=defl)
     torch.cuda.synchronize()
@@ -400,8 +396,8 @@ def ours(args):
     clocks = sampler.stop()
     mem_gb = device_memory_gb(torch)
     # the reported kernels, timed by per-launch CUDA events on their stream over further passes of
-    # the window's first `aux` steps (event pairs go around single launches, so the V-cycle and
-    # the Arnoldi steps are not replayed from CUDA graphs in these passes)
+    # the same steps (event pairs go around single launches, so the V-cycle and the Arnoldi steps
+    # are not replayed from CUDA graphs in these passes)
     rewind(prob)
     _, _, _, prof = measure(prob, torch, aux, args.rtol, kernel_class=1, deflate=defl)
     rewind(prob)
