@@ -34,6 +34,23 @@ def simplex_geometry(coords: np.ndarray, elems: np.ndarray):
     return vol, G
 
 
+def vertex_volumes(coords: np.ndarray, elems: np.ndarray, n_vertices: int, chunk: int = 4_000_000) -> np.ndarray:
+    """M 1 per vertex over the given elements: the row sums of the consistent P1 mass matrix, which
+    for P1 are sum over the elements containing the vertex of |T| / (d+1) (the mass formula above
+    summed over l). Charge per region is then sum_k z_k (M 1) . c^k. Chunked, volumes only, so it
+    runs on meshes of 1e8 elements."""
+    d = coords.shape[1]
+    out = np.zeros(n_vertices)
+    for a in range(0, elems.shape[0], chunk):
+        e = elems[a:a + chunk]
+        x = coords[e]
+        J = x[:, 1:, :] - x[:, :1, :]
+        vol = np.abs(np.linalg.det(J)) / factorial(d)
+        for j in range(d + 1):
+            out += np.bincount(e[:, j], weights=vol / (d + 1), minlength=n_vertices)
+    return out
+
+
 def facet_measure(coords: np.ndarray, facets: np.ndarray) -> np.ndarray:
     """|f| of (d-1)-simplices embedded in R^d (Gram determinant)."""
     x = coords[facets]

@@ -740,6 +740,15 @@ void download_state(const knp_problem* p, std::vector<double>& u) {
     KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 
+// Host buffers go through a device staging copy in the Eq. 4.3 layout ([c_i (3 N_i), phi_i (N_i),
+// c_e (3 N_e), phi_e (N_e)]): one DMA per array (direct from pinned memory) and the same reorder
+// kernels as for device buffers, instead of reordering on the host.
+static double* state_stage(const knp_problem* p) {
+    const int64_t n4 = 4 * (p->N_i + p->N_e);
+    if ((int64_t)p->stage.n < n4) p->stage.alloc(n4);
+    return p->stage.p;
+}
+
 void state_copy_out(const knp_problem* p, bool device, double* c_i, double* phi_i, double* c_e, double* phi_e) {
     const int64_t Ni = p->N_i, Ne = p->N_e, n = Ni + Ne;
     if (device) {
@@ -749,20 +758,18 @@ void state_copy_out(const knp_problem* p, bool device, double* c_i, double* phi_
         KNP_CUDA(cudaStreamSynchronize(p->stream));
         return;
     }
-    std::vector<double> u;
-    download_state(p, u);
-    for (int64_t g = 0; g < n; ++g) {
-        if (g < Ni) {
-            if (c_i)
-                for (int k = 0; k < KI; ++k) c_i[k * Ni + g] = u[4 * g + k];
-            if (phi_i) phi_i[g] = u[4 * g + 3];
-        } else {
-            int64_t j = g - Ni;
-            if (c_e)
-                for (int k = 0; k < KI; ++k) c_e[k * Ne + j] = u[4 * g + k];
-            if (phi_e) phi_e[j] = u[4 * g + 3];
-        }
-    }
+    double* s = state_stage(p);
+    double* seg[4] = {s, s + 3 * Ni, s + 4 * Ni, s + 4 * Ni + 3 * Ne};
+    double* dst[4] = {c_i, phi_i, c_e, phi_e};
+    const int64_t len[4] = {3 * Ni, Ni, 3 * Ne, Ne};
+    count_launch();
+    k_state_out<<<nblk(n), 256, 0, p->stream>>>(p->u.p, Ni, Ne, c_i ? seg[0] : nullptr, phi_i ? seg[1] : nullptr,
+                                                c_e ? seg[2] : nullptr, phi_e ? seg[3] : nullptr);
+    KNP_CUDA(cudaGetLastError());
+    for (int a = 0; a < 4; ++a)
+        if (dst[a] && len[a])
+            KNP_CUDA(cudaMemcpyAsync(dst[a], seg[a], len[a] * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 
 void state_copy_in(knp_problem* p, bool device, const double* c_i, const double* phi_i, const double* c_e,
@@ -774,21 +781,18 @@ void state_copy_in(knp_problem* p, bool device, const double* c_i, const double*
         KNP_CUDA(cudaGetLastError());
         return;
     }
-    std::vector<double> u;
-    download_state(p, u);
-    for (int64_t g = 0; g < n; ++g) {
-        if (g < Ni) {
-            if (c_i)
-                for (int k = 0; k < KI; ++k) u[4 * g + k] = c_i[k * Ni + g];
-            if (phi_i) u[4 * g + 3] = phi_i[g];
-        } else {
-            int64_t j = g - Ni;
-            if (c_e)
-                for (int k = 0; k < KI; ++k) u[4 * g + k] = c_e[k * Ne + j];
-            if (phi_e) u[4 * g + 3] = phi_e[j];
-        }
-    }
-    KNP_CUDA(cudaMemcpyAsync(p->u.p, u.data(), u.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    double* s = state_stage(p);
+    double* seg[4] = {s, s + 3 * Ni, s + 4 * Ni, s + 4 * Ni + 3 * Ne};
+    const double* src[4] = {c_i, phi_i, c_e, phi_e};
+    const int64_t len[4] = {3 * Ni, Ni, 3 * Ne, Ne};
+    for (int a = 0; a < 4; ++a)
+        if (src[a] && len[a])
+            KNP_CUDA(cudaMemcpyAsync(seg[a], src[a], len[a] * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    count_launch();
+    k_state_in<<<nblk(n), 256, 0, p->stream>>>(p->u.p, Ni, Ne, c_i ? seg[0] : nullptr, phi_i ? seg[1] : nullptr,
+                                               c_e ? seg[2] : nullptr, phi_e ? seg[3] : nullptr);
+    KNP_CUDA(cudaGetLastError());
+    // the caller's host buffers may be reused as soon as this returns
     KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 

@@ -169,6 +169,7 @@ struct knp_problem {
     knp::DArray<double> sinv;            // 1/sqrt(diag P_0) (set by knp_amg_setup)
     knp::DArray<double> svec;            // sqrt(diag P_0)
     knp::DArray<double> swt;             // weights of the stopping test: svec, 0 on the pinned phi_e
+    mutable knp::DArray<double> stage;   // [4 n] staging copy of host state buffers (Eq. 4.3 layout)
     knp::DArray<double> src;             // bulk source f_r^k at the nodes [n_nodes][4] (empty = none)
 
     knp::Profiler prof;

@@ -346,8 +346,8 @@ class Problem:
     def assemble_step(self):
         _check(_lib.knp_assemble_step(self.handle))
 
-    def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=1,
-                  cheb_ratio=4.0, theta_coarse=0.0, p_drop=0.0, host_setup=False, inner_cg_max_it=0,
+    def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=2,
+                  cheb_ratio=3.0, theta_coarse=0.0, p_drop=0.0, host_setup=False, inner_cg_max_it=0,
                   inner_cg_rtol=1e-8):
         """inner_cg_max_it > 0 selects CG(P_0) (V-cycle-preconditioned CG per field block of P_0,
         to inner_cg_rtol) instead of one V-cycle."""

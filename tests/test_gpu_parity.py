@@ -540,3 +540,62 @@ def test_paper_model_a_iterations(nx):
     its = [prob.step(1, rtol=1e-6, stop_test=KNP_TEST_PAPER)[0]["iterations"] for _ in range(10)]
     print(f"Model A N_x = {nx}: iterations {its}, mean {np.mean(its):.2f} (Table 3: {printed})")
     assert np.mean(its) <= 1.5 * printed, its
+
+
+@pytest.mark.slow
+def test_full_size_2d_16_cells_states_match_oracle():
+    """The differentiation workload's forward run at its full size (256^2 mesh, 16 cells, per-facet
+    g_K, 274,052 unknowns; FP64, rtol 1e-10 as configured): the first three steps match the oracle's
+    direct solves at 1e-8 relative l2 on the concentrations and on the potentials."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(4)
+    pb, ref = oracle_run(cfg, 3, "direct")
+    _, prob = problem_from_config(cfg)
+    assert prob.n_dof == 274052
+    prob.amg_setup()
+    for n in range(1, 4):
+        prob.step(1, rtol=1e-10)
+        ec, ep = rel_errors(prob.state_get(), ref[n])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep)
+
+
+@pytest.mark.slow
+def test_headline_workload_conserves_charge_at_full_size():
+    """The 512-cell 256^3 workload (73,078,172 unknowns) in the bench's configuration (FP32 hierarchy,
+    FGMRES at rtol 1e-8, coarse correction): the oracle cannot solve it, so a property that holds
+    at any size is checked instead. Summing the concentration equations with v = 1 over a cell, or
+    over the extracellular space, leaves only the membrane fluxes, which cancel (Section 2.2): the
+    charge sum_k z_k 1^T M_r c_r^k of every cell and of the extracellular space is the same after
+    three steps as before, up to the solver tolerance. 1^T M_r is the lumped mass (the oracle's
+    vertex_volumes)."""
+    from oracle import fem
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(5)
+    m = cfg.mesh
+    mesh, prob = problem_from_config(cfg)
+    assert prob.n_dof == 73078172
+    ni, ne = mesh.nodes()
+    nv = m.coords.shape[0]
+    tag = m.elem_tag
+    mi = fem.vertex_volumes(m.coords, m.elems[tag > 0], nv)[ni]
+    me = fem.vertex_volumes(m.coords, m.elems[tag == 0], nv)[ne]
+    vcell = np.zeros(nv, np.int64)
+    inner = m.elems[tag > 0]
+    for j in range(inner.shape[1]):
+        vcell[inner[:, j]] = tag[tag > 0]
+    cell = vcell[ni]
+    z = np.asarray(cfg.params["z"])
+
+    def charges(st):
+        qi = sum(z[k] * mi * st["c_i"][k] for k in range(3))
+        return np.bincount(cell, weights=qi), sum(z[k] * (me * st["c_e"][k]).sum() for k in range(3))
+
+    s0 = prob.state_get()
+    scale = sum((me * s0["c_e"][k]).sum() for k in range(3))
+    q0 = charges(s0)
+    prob.amg_setup(precision=1)
+    its = [prob.step(1, rtol=1e-8)[0]["iterations"] for _ in range(3)]
+    q1 = charges(prob.state_get())
+    print("iterations", its, "charge change per cell", np.abs(q1[0] - q0[0]).max() / scale,
+          "extracellular", abs(q1[1] - q0[1]) / scale)
+    assert np.abs(q1[0] - q0[0]).max() < 1e-7 * scale and abs(q1[1] - q0[1]) < 1e-7 * scale

@@ -122,3 +122,19 @@ def test_global_matrix_identities(d, nx):
     c = m.coords[t.nodes_e, 0] * 1e6 + 2.0
     Ak = fem.weighted_stiffness(cache, c, en, t.N_e)
     assert np.abs(Ak @ np.ones(t.N_e)).max() < 1e-12 * np.abs(Ak).max()
+
+
+def test_vertex_volumes_are_the_mass_row_sums():
+    """vertex_volumes equals M 1 of the assembled consistent mass matrix (chunked or not) and sums
+    to the region's volume."""
+    from synth import make_config
+    from oracle import fem
+    cfg = make_config(2).with_nx(6)
+    m = cfg.mesh
+    n = m.coords.shape[0]
+    loc = np.arange(n)
+    M, _, _ = fem.assemble_bulk(m.coords, m.elems, loc, n)
+    for chunk in (10_000_000, 97):
+        v = fem.vertex_volumes(m.coords, m.elems, n, chunk=chunk)
+        assert np.allclose(v, np.asarray(M.sum(axis=1)).ravel(), rtol=1e-12, atol=0)
+    assert abs(v.sum() - cfg.length ** 3) < 1e-12 * cfg.length ** 3
