@@ -282,6 +282,11 @@ typedef struct {
                              comparing iteration counts with Tables 3 and 4 */
     double phi_e_floor;   /* with phi_e_group: the phi_e part is tested against
                              max(rtol ||S phi_e||, phi_e_floor ||S phi||); <= 0 selects 1e-14 */
+    int32_t x0_extrapolate;  /* 1: start from x_0 = 2 u_{n-1} - u_{n-2} (linear extrapolation in time)
+                                instead of the paper's x_0 = u_{n-1}, when the previous knp_solve on
+                                this problem also extrapolated and succeeded and no knp_state_set came
+                                between; otherwise x_0 = u_{n-1}. Changes the iteration count, not the
+                                stopping test. Keeps one more state vector on the device. */
 } knp_solve_opts;
 
 enum { KNP_TEST_SCALED = 0, KNP_TEST_PAPER = 1 };
@@ -294,7 +299,7 @@ typedef struct {
     int64_t inner_iterations;  /* inner CG iterations of CG(P_0) over the solve (0 for AMG(P_0)) */
 } knp_solve_stats;
 
-/* FGMRES(restart), FP64, x_0 = u_{n-1} (Section 6.2), right-preconditioned by
+/* FGMRES(restart), FP64, x_0 = u_{n-1} (Section 6.2; or extrapolated, x0_extrapolate), right-preconditioned by
  * one V-cycle on P_0. On success the step is committed: the state becomes
  * (u_n, w_n) and t advances by dt. KNP_ERR_NOT_CONVERGED keeps the last
  * iterate in u and does not advance w or t. */

@@ -241,6 +241,9 @@ knp_status knp_solve(knp_problem* p, const knp_solve_opts* o, knp_solve_stats* s
         KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_solve called before knp_amg_setup");
         KNP_REQUIRE(o->rtol > 0 && o->restart >= 1 && o->max_it >= 1, KNP_ERR_INVALID_ARG, "solve options out of range");
         knp_solve_stats s{};
+        const bool extrapolate = o->x0_extrapolate != 0;
+        if (extrapolate) initial_guess(p, p->hist_valid);
+        p->hist_valid = false;
         det = fgmres(p, *o, s, p->u.p, p->f.p, false);
         if (stats) *stats = s;
         if (det.code == KNP_OK) {
@@ -249,6 +252,7 @@ knp_status knp_solve(knp_problem* p, const knp_solve_opts* o, knp_solve_stats* s
             p->t += p->sp.dt;
             p->step_index++;
             p->assembled = false;
+            p->hist_valid = extrapolate;
         }
     });
     if (st == KNP_OK && det.code != KNP_OK) {
@@ -303,6 +307,7 @@ knp_status knp_state_set(knp_problem* p, knp_memspace space, const double* c_i, 
         KNP_CUDA(cudaStreamSynchronize(p->stream));
         p->t = t;
         p->assembled = false;
+        p->hist_valid = false;
     });
 }
 

@@ -139,6 +139,15 @@ __global__ void k_state_in(double* u, int64_t N_i, int64_t N_e, const double* c_
     }
 }
 
+// x_0 of a solve: u <- 2 u_{n-1} - u_{n-2} (extrapolate) or u_{n-1}; h <- u_{n-1}
+__global__ void k_initial_guess(int64_t n4, double* __restrict__ u, double* __restrict__ h, int extrapolate) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    const double o = u[i];
+    if (extrapolate) u[i] = 2.0 * o - h[i];
+    h[i] = o;
+}
+
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -738,6 +747,17 @@ void build_problem_stiffness(knp_problem* P, std::vector<double>& elA, std::vect
 void download_state(const knp_problem* p, std::vector<double>& u) {
     p->u.download(u, p->stream);
     KNP_CUDA(cudaStreamSynchronize(p->stream));
+}
+
+void initial_guess(knp_problem* p, bool extrapolate) {
+    const int64_t n4 = 4 * (p->N_i + p->N_e);
+    if ((int64_t)p->u_hist.n < n4) {
+        p->u_hist.alloc(n4);
+        extrapolate = false;
+    }
+    count_launch();
+    k_initial_guess<<<nblk(n4), 256, 0, p->stream>>>(n4, p->u.p, p->u_hist.p, extrapolate ? 1 : 0);
+    KNP_CUDA(cudaGetLastError());
 }
 
 // Host buffers go through a device staging copy in the Eq. 4.3 layout ([c_i (3 N_i), phi_i (N_i),

@@ -165,6 +165,8 @@ struct knp_problem {
 
     // vectors [n_nodes][4]
     knp::DArray<double> u;               // state u_{n-1} / u_n
+    knp::DArray<double> u_hist;          // u_{n-2} for an extrapolated x_0 (allocated on first use)
+    bool hist_valid = false;             // u_hist holds the state one step before u
     knp::DArray<double> f;               // right-hand side f_n
     knp::DArray<double> sinv;            // 1/sqrt(diag P_0) (set by knp_amg_setup)
     knp::DArray<double> svec;            // sqrt(diag P_0)
@@ -206,4 +208,7 @@ void op_apply(knp_problem* p, const double* x, double* y, const double* rowscale
 // the static per-ion values of the forward product (after the pattern and m, a are on the device)
 void op_prepare(knp_problem* p, cudaStream_t st);
 void download_state(const knp_problem* p, std::vector<double>& u);
+// x_0 of the next solve in u: 2 u_{n-1} - u_{n-2} when extrapolating from a valid history,
+// u_{n-1} otherwise; u_hist becomes u_{n-1}
+void initial_guess(knp_problem* p, bool extrapolate);
 }  // namespace knp

@@ -79,7 +79,8 @@ class AmgSetupRecord(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32), ("phi_e_group", C.c_int32),
-                ("deflate", C.c_int32), ("stop_test", C.c_int32), ("phi_e_floor", C.c_double)]
+                ("deflate", C.c_int32), ("stop_test", C.c_int32), ("phi_e_floor", C.c_double),
+                ("x0_extrapolate", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -356,18 +357,21 @@ class Problem:
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
     def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False, deflate=True, stop_test=KNP_TEST_SCALED,
-              phi_e_floor=0.0):
+              phi_e_floor=0.0, x0_extrapolate=False):
         """deflate: the coarse correction of the potentials' near-null modes around P_0^{-1};
-        stop_test: KNP_TEST_SCALED (per-group scaled test) or KNP_TEST_PAPER (Section 6.2's)."""
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), int(stop_test), float(phi_e_floor))
+        stop_test: KNP_TEST_SCALED (per-group scaled test) or KNP_TEST_PAPER (Section 6.2's);
+        x0_extrapolate: x_0 = 2 u_{n-1} - u_{n-2} after a previous extrapolating solve."""
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), int(stop_test), float(phi_e_floor),
+                      int(x0_extrapolate))
         s = SolveStats()
         _check(_lib.knp_solve(self.handle, C.byref(o), C.byref(s)))
         return {"iterations": s.iterations, "restarts": s.restarts, "true_relres": s.true_relres, "ms": s.ms,
                 "inner_iterations": s.inner_iterations}
 
     def step(self, nsteps=1, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False, deflate=True,
-             stop_test=KNP_TEST_SCALED, phi_e_floor=0.0):
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), int(stop_test), float(phi_e_floor))
+             stop_test=KNP_TEST_SCALED, phi_e_floor=0.0, x0_extrapolate=False):
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), int(stop_test), float(phi_e_floor),
+                      int(x0_extrapolate))
         st = (StepStats * max(nsteps, 1))()
         _check(_lib.knp_step(self.handle, nsteps, C.byref(o), st))
         return [{"iterations": st[i].iterations, "true_relres": st[i].true_relres} for i in range(nsteps)]
@@ -430,7 +434,7 @@ class Problem:
     def adjoint_step(self, u_n, dLdu_n, rtol=1e-10, restart=30, max_it=1000, phi_e_group=True, phi_e_floor=0.0,
                      deflate=True):
         """u_n, dLdu_n in the Eq. 4.3 order: numpy arrays (host) or CUDA tensors (device)."""
-        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), KNP_TEST_SCALED, float(phi_e_floor))
+        o = SolveOpts(rtol, restart, max_it, int(phi_e_group), int(deflate), KNP_TEST_SCALED, float(phi_e_floor), 0)
         s = SolveStats()
         if hasattr(u_n, "data_ptr"):
             _check(_lib.knp_adjoint_step(self.handle, KNP_DEVICE, C.c_void_p(u_n.data_ptr()),

@@ -118,6 +118,26 @@ def test_config2_horizon_past_the_stimulus(precision):
 
 
 @pytest.mark.slow
+def test_extrapolated_initial_guess_matches_oracle():
+    """x_0 = 2 u_{n-1} - u_{n-2} in place of u_{n-1} changes where FGMRES starts, not what it
+    stops at: the 3D HH workload's 24^3 version still matches the oracle at 1e-8 at every one of 26
+    steps (rtol 1e-10, FP64 hierarchy), also after a knp_state_set in the middle of the run (which
+    drops the history, so that the next start is u_{n-1} of the new state)."""
+    from paper_2403_04491_gb300 import problem_from_config
+    cfg = make_config(2).with_nx(24)
+    pb, ref = _horizon_ref()
+    _, prob = problem_from_config(cfg)
+    prob.amg_setup(precision=0)
+    for n in range(1, 27):
+        if n == 14:
+            r = ref[13]
+            prob.state_set(r.c_i, r.phi_i, r.c_e, r.phi_e, r.w, r.t)
+        prob.step(1, rtol=1e-10, x0_extrapolate=True)
+        ec, ep = rel_errors(prob.state_get(), ref[n])
+        assert ec <= TOL and ep <= TOL, (n, ec, ep)
+
+
+@pytest.mark.slow
 def test_config3_subset_125_cells_mixed():
     """The 125-cell workload at its 32^3 version (192,748 unknowns) in its own configuration: FP32
     hierarchy under FP64 FGMRES at rtol 1e-8, three steps. The error against the oracle is held to
