@@ -23,7 +23,9 @@
 // region, plus its cross-region entries times the constants of their cells. Those row sums are
 // formed once per step (RS, three values per node), E is an arrowhead matrix (cells couple only
 // to the extracellular space) solved by its Schur complement on the device, and each application
-// adds a gather, a small solve, a right-hand-side pass and an update: about 0.2 KB per node.
+// adds a gather and a small solve; the right-hand-side pass and the update run inside the
+// V-cycle's first and last kernels (the transposed form and CG(P_0) keep them as separate passes,
+// about 0.2 KB per node).
 // Sums are taken in a fixed order (no atomics), so the result is reproducible bit for bit.
 #include <algorithm>
 #include <map>
@@ -362,12 +364,31 @@ void deflated_precond_apply(knp_problem* p, const double* v, const double* s, do
     cudaStream_t st = p->stream;
     const int64_t n = p->n_nodes, nx = (int64_t)p->h_xcol.size();
     const double* zc = p->sp.z;
-    count_launch(3);
+    count_launch(2);
     k_defl_gather<<<d.nc + EXT_BLOCKS, DT, 0, st>>>(d.nc, d.cptr.p, d.cnodes.p, p->N_i, n, p->pin, v, s, d.g.p,
                                                     d.part.p);
     // Z^T A^T Z = E^T: the same Schur complement, E_je and E_ej exchanged
     k_defl_solve<<<1, DT, 0, st>>>(d.nc, d.part.p, d.g.p, d.Ejj.p, transpose ? d.Eej.p : d.Eje.p,
                                    transpose ? d.Eje.p : d.Eej.p, d.Ee.p, d.y.p);
+    if (!transpose && p->amg->inner_cg_max_it == 0) {
+        // one V-cycle: its first kernel forms s .* v - A Z y and its output kernel adds Z y
+        DeflFuse df;
+        df.rgrp = d.rgrp.p;
+        df.RS = d.RS.p;
+        df.xptr = p->xptr.p;
+        df.xg = d.xg.p;
+        df.xe = p->xe.p;
+        df.y = d.y.p;
+        df.n_cross = nx;
+        df.N_i = p->N_i;
+        df.pin = p->pin;
+        df.ext_group = d.nc;
+        for (int q = 0; q < 3; ++q) df.z[q] = zc[q];
+        KNP_CUDA(cudaGetLastError());
+        vcycle_apply(p, v, s, z, &df);
+        return;
+    }
+    count_launch();
     if (transpose)
         k_defl_rhs_t<<<nbk(n, 128), 128, 0, st>>>(n, p->N_i, p->pin, d.rgrp.p, d.RS.p, d.RSa.p, p->xtptr.p,
                                                   p->xtidx.p, d.xtg.p, p->xe.p, nx, zc[0], zc[1], zc[2], p->sp.reg[0],

@@ -108,14 +108,41 @@ __device__ __forceinline__ double pick4(const double c[4], int f) {
     return f == 0 ? c[0] : f == 1 ? c[1] : f == 2 ? c[2] : c[3];
 }
 
-// first Chebyshev step from x = 0: d = c2 D^-1 b, x = d. On the finest level b = s .* v (double input).
+// The coarse correction's input at node i: t = s .* v - (A Z y)_i. Row i of A Z y: its same-region
+// phi columns hold its own group's constant (the row sums RS), its cross-region entries their
+// groups' constants; the potential row is sum_k z_k of the concentration rows' terms, and the
+// pinned potential row (the identity) gives 0.
+__device__ __forceinline__ void defl_input(int64_t i, const double* __restrict__ v, const double* __restrict__ s,
+                                           const DeflFuse& df, double t[4]) {
+    const double yr = df.y[i < df.N_i ? df.rgrp[i] : df.ext_group];
+    double ae[3];
+    for (int q = 0; q < 3; ++q) ae[q] = df.RS[3 * i + q] * yr;
+    for (int u = df.xptr[i]; u < df.xptr[i + 1]; ++u) {
+        const int gq = df.xg[u];
+        if (gq < 0) continue;
+        const double yc = df.y[gq];
+        for (int q = 0; q < 3; ++q) ae[q] += df.xe[q * df.n_cross + u] * yc;
+    }
+    double out3 = df.z[0] * ae[0] + df.z[1] * ae[1] + df.z[2] * ae[2];
+    if (i == df.pin) out3 = 0.0;
+    for (int q = 0; q < 3; ++q) t[q] = s[4 * i + q] * v[4 * i + q] - ae[q];
+    t[3] = s[4 * i + 3] * v[4 * i + 3] - out3;
+}
+
+// first Chebyshev step from x = 0: d = c2 D^-1 b, x = d. On the finest level b = s .* v (double
+// input), or s .* v - A Z y inside the coarse correction (df.y set).
 template <class T>
 __global__ void k_cheb_first(int64_t n, const double* __restrict__ v, const double* __restrict__ s, T* __restrict__ b,
-                             const T* __restrict__ dinv, Coef4 c, T* __restrict__ x, T* __restrict__ d) {
+                             const T* __restrict__ dinv, Coef4 c, T* __restrict__ x, T* __restrict__ d, DeflFuse df) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     V4<T> bb;
-    if (v) {
+    if (v && df.y) {
+        double t[4];
+        defl_input(i, v, s, df, t);
+        for (int f = 0; f < 4; ++f) bb.v[f] = (T)t[f];
+        bb.store(b + 4 * i);
+    } else if (v) {
         for (int f = 0; f < 4; ++f) bb.v[f] = (T)(s[4 * i + f] * v[4 * i + f]);
         bb.store(b + 4 * i);
     } else {
@@ -248,6 +275,20 @@ __global__ void k_to_double(int64_t n4, const T* __restrict__ x, double* __restr
     if (i < n4) z[i] = (double)x[i];
 }
 
+// z = x + Z y: the V-cycle's output in FP64, every potential but the pinned one raised by its
+// group's constant of the coarse correction
+template <class T>
+__global__ void k_out_defl(int64_t n, const T* __restrict__ x, double* __restrict__ z, DeflFuse df) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const V4<T> xx = V4<T>::load(x + 4 * r);
+    double o3 = (double)xx.v[3];
+    if (r != df.pin) o3 += df.y[r < df.N_i ? df.rgrp[r] : df.ext_group];
+    double2* zp = reinterpret_cast<double2*>(z + 4 * r);
+    zp[0] = make_double2((double)xx.v[0], (double)xx.v[1]);
+    zp[1] = make_double2((double)xx.v[2], o3);
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <class T>
@@ -341,8 +382,16 @@ AmgHierarchy::~AmgHierarchy() {
     delete static_cast<AmgDev<float>*>(h32);
 }
 
+// A level's operator is stored sliced-ELL (one thread per row, the value loads of a warp
+// contiguous) unless padding every slice to its longest row would store more than this many
+// entries per nonzero; then CSR with a few lanes per row. Measured on the 512-cell 256^3
+// workload, whose first coarse level has 58 entries per row: sliced ELL there (and on the
+// second, 39 per row) is 2.4% faster per FGMRES iteration than CSR.
+constexpr double SELL_MAX_STORED = 2.0;
+
+// sliced ELL of a host CSR level; false (nothing done) if the padding exceeds SELL_MAX_STORED
 template <class T>
-static void upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
+static bool upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
     const int64_t n = A.n_rows;
     int64_t ns = (n + SELL_C - 1) / SELL_C;
     std::vector<int64_t> sp(ns + 1, 0);
@@ -351,6 +400,7 @@ static void upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
         for (int64_t r = s * SELL_C; r < std::min(n, (s + 1) * SELL_C); ++r) w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
         sp[s + 1] = sp[s] + w * SELL_C;
     }
+    if ((double)sp[ns] > SELL_MAX_STORED * (double)std::max<int64_t>(A.nnz(), 1)) return false;
     std::vector<int32_t> col(sp[ns]);
     std::vector<T> val(4 * sp[ns], T(0));
     for (int64_t s = 0; s < ns; ++s) {
@@ -373,6 +423,7 @@ static void upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
     L.sp.upload(sp, st);
     L.scol.upload(col, st);
     L.sval.upload(val, st);
+    return true;
 }
 
 // work vectors of a level and the coefficients of its Chebyshev steps (Saad's three-term
@@ -409,11 +460,8 @@ static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, c
         const int64_t n = HL.A.n_rows;
         L->n = n;
         L->nnz = HL.A.nnz();
-        L->sell = (double)L->nnz / (double)std::max<int64_t>(n, 1) <= 24.0;
-        if (L->sell)
-            upload_sell(*L, HL.A, st);
-        else
-            L->A.upload(HL.A, st);
+        L->sell = upload_sell(*L, HL.A, st);
+        if (!L->sell) L->A.upload(HL.A, st);
         L->dinv.upload(cast_vec<T>(HL.dinv), st);
         for (int f = 0; f < 4; ++f) {
             L->lmax[f] = HL.lmax[f];
@@ -462,14 +510,19 @@ __global__ void k_sell_fill(int64_t n, int64_t ns, const int64_t* __restrict__ p
     }
 }
 
+// sliced ELL of a device CSR level (its CSR arrays released); false (nothing done) if the padding
+// exceeds SELL_MAX_STORED
 template <class T>
-static void take_sell(DevLevel<T>& L, DevCsr4d& A, cudaStream_t st) {
+static bool take_sell(DevLevel<T>& L, DevCsr4d& A, cudaStream_t st) {
     const int64_t n = A.n_rows, ns = (n + SELL_C - 1) / SELL_C;
     DArray<int64_t> w;
     w.alloc(std::max<int64_t>(ns, 1));
     k_sell_widths<<<nblk(ns, 256), 256, 0, st>>>(n, ns, A.ptr.p, w.p);
-    L.sp.alloc(ns + 1);
-    const int64_t total = device_exclusive_scan(w.p, L.sp.p, ns, st);
+    DArray<int64_t> sp;
+    sp.alloc(ns + 1);
+    const int64_t total = device_exclusive_scan(w.p, sp.p, ns, st);
+    if ((double)total > SELL_MAX_STORED * (double)std::max<int64_t>(A.nnz, 1)) return false;
+    L.sp = std::move(sp);
     L.scol.alloc(std::max<int64_t>(total, 1));
     L.sval.alloc(std::max<int64_t>(4 * total, 1));
     k_sell_fill<T><<<nblk(ns * SELL_C, 128), 128, 0, st>>>(n, ns, A.ptr.p, A.col.p, A.val.p, L.sp.p, L.scol.p, L.sval.p);
@@ -477,6 +530,7 @@ static void take_sell(DevLevel<T>& L, DevCsr4d& A, cudaStream_t st) {
     A.ptr.release();
     A.col.release();
     A.val.release();
+    return true;
 }
 
 // The same device hierarchy as upload_hierarchy, taken over from the GPU setup level by level
@@ -489,11 +543,8 @@ static void take_hierarchy(AmgDev<T>& D, GpuHierarchy& H, int degree, cudaStream
         const int64_t n = G->A.n_rows;
         L->n = n;
         L->nnz = G->A.nnz;
-        L->sell = (double)L->nnz / (double)std::max<int64_t>(n, 1) <= 24.0;
-        if (L->sell)
-            take_sell(*L, G->A, st);
-        else
-            L->A.take(G->A, st);
+        L->sell = take_sell(*L, G->A, st);
+        if (!L->sell) L->A.take(G->A, st);
         take_values(L->dinv, G->dinv, 4 * n, st);
         for (int f = 0; f < 4; ++f) {
             L->lmax[f] = G->lmax[f];
@@ -602,18 +653,19 @@ static void csr_apply(DevCsr4<T>& M, const T* x, T* y, int accumulate, cudaStrea
 
 template <class T>
 static void smooth(DevLevel<T>& L, const std::vector<Coef4>& cs, int degree, bool zero_start, const double* v,
-                   const double* s, Profiler* pr, bool fine, cudaStream_t st) {
+                   const double* s, const DeflFuse& df, Profiler* pr, bool fine, cudaStream_t st) {
     int k0 = 0;
     if (zero_start) {
         count_launch();
-        k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, cs[0], L.x.p, L.d.p);
+        k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, cs[0], L.x.p, L.d.p, df);
         k0 = 1;
     }
     for (int k = k0; k < degree; ++k) cheb_step(L, cs[k], pr, fine, st);
 }
 
 template <class T>
-static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, Profiler* pr, cudaStream_t st) {
+static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, const DeflFuse& df, Profiler* pr,
+                       cudaStream_t st) {
     DevLevel<T>& L = *D.L[l];
     const int last = (int)D.L.size() - 1;
     if (l == last) {
@@ -621,31 +673,40 @@ static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, Pr
             // single-level hierarchy: build b from the scaled input first
             Coef4 c0{};
             count_launch();
-            k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, c0, L.x.p, L.d.p);
+            k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, L.b.p, L.dinv.p, c0, L.x.p, L.d.p, df);
         }
         count_launch();
         k_coarse<T><<<nblk(4 * D.nc * 32, 256), 256, 0, st>>>(D.nc, D.cinv.p, L.b.p, L.x.p);
         return;
     }
     DevLevel<T>& C = *D.L[l + 1];
-    smooth(L, D.coef[l], D.degree, true, v, s, pr, l == 0, st);
+    smooth(L, D.coef[l], D.degree, true, v, s, df, pr, l == 0, st);
     residual(L, pr, l == 0, st);
     csr_apply(L.R, L.r.p, C.b.p, 0, st);
-    vcycle_rec(D, l + 1, nullptr, nullptr, pr, st);
+    vcycle_rec(D, l + 1, nullptr, nullptr, DeflFuse{}, pr, st);
     csr_apply(L.P, C.x.p, L.x.p, 1, st);
-    smooth(L, D.coef[l], D.degree, false, nullptr, nullptr, pr, l == 0, st);
+    smooth(L, D.coef[l], D.degree, false, nullptr, nullptr, DeflFuse{}, pr, l == 0, st);
 }
 
-static void vcycle_launch(knp_problem* p, const double* v, const double* s, double* z, cudaStream_t st) {
+static void vcycle_launch(knp_problem* p, const double* v, const double* s, double* z, const DeflFuse& df,
+                          cudaStream_t st) {
     if (p->amg->h32) {
         auto& D = *static_cast<AmgDev<float>*>(p->amg->h32);
-        vcycle_rec(D, 0, v, s, &p->prof, st);
+        vcycle_rec(D, 0, v, s, df, &p->prof, st);
         count_launch();
-        k_to_double<float><<<nblk(4 * D.L[0]->n, 256), 256, 0, st>>>(4 * D.L[0]->n, D.L[0]->x.p, z);
+        if (df.y)
+            k_out_defl<float><<<nblk(D.L[0]->n, 256), 256, 0, st>>>(D.L[0]->n, D.L[0]->x.p, z, df);
+        else
+            k_to_double<float><<<nblk(4 * D.L[0]->n, 256), 256, 0, st>>>(4 * D.L[0]->n, D.L[0]->x.p, z);
     } else {
         auto& D = *static_cast<AmgDev<double>*>(p->amg->h64);
-        vcycle_rec(D, 0, v, s, &p->prof, st);
-        KNP_CUDA(cudaMemcpyAsync(z, D.L[0]->x.p, 4 * D.L[0]->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        vcycle_rec(D, 0, v, s, df, &p->prof, st);
+        if (df.y) {
+            count_launch();
+            k_out_defl<double><<<nblk(D.L[0]->n, 256), 256, 0, st>>>(D.L[0]->n, D.L[0]->x.p, z, df);
+        } else {
+            KNP_CUDA(cudaMemcpyAsync(z, D.L[0]->x.p, 4 * D.L[0]->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
     }
 }
 
@@ -664,27 +725,29 @@ void p0_apply(knp_problem* p, const double* x, double* y) {
     KNP_CUDA(cudaGetLastError());
 }
 
-void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z) {
+void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z, const DeflFuse* dfp) {
     KNP_REQUIRE(p->amg, KNP_ERR_STATE, "knp_amg_setup has not been called");
     AmgHierarchy& H = *p->amg;
     cudaStream_t st = p->stream;
+    const DeflFuse df = dfp ? *dfp : DeflFuse{};
     if (!H.use_graphs || p->prof.active >= 0) {
         ProfScope ps(&p->prof, KC_VCYCLE, st);
-        vcycle_launch(p, v, s, z, st);
+        vcycle_launch(p, v, s, z, df, st);
         KNP_CUDA(cudaGetLastError());
         return;
     }
     if (!H.gstream) {
         KNP_CUDA(cudaStreamCreateWithFlags(&H.gstream, cudaStreamNonBlocking));
     }
-    auto key = std::make_tuple(v, s, z);
+    // the correction's arrays are fixed per problem, so its y pointer identifies them
+    auto key = std::make_tuple(v, s, z, df.y);
     auto it = H.graphs.find(key);
     if (it == H.graphs.end()) {
         VcycleGraph g;
         int64_t before = g_launches.load();
         KNP_CUDA(cudaStreamBeginCapture(H.gstream, cudaStreamCaptureModeThreadLocal));
         try {
-            vcycle_launch(p, v, s, z, H.gstream);
+            vcycle_launch(p, v, s, z, df, H.gstream);
         } catch (...) {
             cudaGraph_t tmp;
             cudaStreamEndCapture(H.gstream, &tmp);
@@ -800,7 +863,7 @@ static void na_vcycle_rec(AmgDev<T>& D, std::vector<NaWork<T>>& W, int l, const 
         if (v) {
             Coef4 c0{};
             count_launch();
-            k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, c0, w.x, w.d);
+            k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, c0, w.x, w.d, DeflFuse{});
         }
         count_launch();
         k_coarse<T><<<nblk(4 * D.nc * 32, 256), 256, 0, st>>>(D.nc, D.cinv.p, w.b, w.x);
@@ -810,7 +873,7 @@ static void na_vcycle_rec(AmgDev<T>& D, std::vector<NaWork<T>>& W, int l, const 
     NaWork<T>& wc = W[l + 1];
     const std::vector<Coef4>& cs = D.coef[l];
     count_launch();
-    k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, cs[0], w.x, w.d);
+    k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, cs[0], w.x, w.d, DeflFuse{});
     for (int k = 1; k < D.degree; ++k) na_cheb_step(L, w, cs[k], st);
     count_launch();
     if (L.sell) {
