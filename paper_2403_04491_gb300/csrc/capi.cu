@@ -183,6 +183,9 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
                         o->cheb_degree >= 1 && o->cheb_degree <= 8 && o->cheb_ratio > 1 && o->theta_coarse < 1 &&
                         o->p_drop >= 0 && o->p_drop < 1,
                     KNP_ERR_INVALID_ARG, "AMG options out of range");
+        KNP_REQUIRE(o->cheb_degree_pre <= 8, KNP_ERR_INVALID_ARG, "AMG options out of range");
+        // CG(P_0) needs a symmetric preconditioner: as many steps before the correction as after
+        const int pre = o->inner_cg_max_it > 0 ? o->cheb_degree : (o->cheb_degree_pre >= 1 ? o->cheb_degree_pre : 1);
         KNP_REQUIRE(o->inner_cg_max_it >= 0 && (o->inner_cg_max_it == 0 || (o->inner_cg_rtol > 0 && o->inner_cg_rtol < 1)),
                     KNP_ERR_INVALID_ARG, "inner CG options out of range");
         KNP_REQUIRE(o->inner_cg_max_it == 0 || o->precision == KNP_PREC_FP64, KNP_ERR_INVALID_ARG,
@@ -208,12 +211,12 @@ knp_status knp_amg_setup(knp_problem* p, const knp_amg_opts* o) {
             strength.release();
             HostHierarchy H;
             amg_build(A0h, sh, p->pin, so, H);
-            amg_upload(p, H, o->precision, o->cheb_degree);
+            amg_upload(p, H, o->precision, o->cheb_degree, pre);
         } else {
             const char* cap = std::getenv("KNP_AMG_SHORT_ROW_MAX");
             GpuHierarchy G;
             amg_build_gpu(A0, strength, p->pin, so, G, st, cap ? std::atoi(cap) : 0);
-            amg_take_gpu(p, G, o->precision, o->cheb_degree);
+            amg_take_gpu(p, G, o->precision, o->cheb_degree, pre);
         }
         p->amg->inner_cg_max_it = o->inner_cg_max_it;
         p->amg->inner_cg_rtol = o->inner_cg_rtol;

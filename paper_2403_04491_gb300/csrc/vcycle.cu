@@ -353,11 +353,11 @@ template <class T>
 struct DevLevel {
     int64_t n = 0, nnz = 0;
     bool sell = false;
-    // sliced ELL (finest level)
+    // sliced ELL (every level whose padding is small)
     DArray<int64_t> sp;
     DArray<int32_t> scol;
     DArray<T> sval;
-    // CSR (coarser levels)
+    // CSR (levels too irregular for sliced ELL)
     DevCsr4<T> A;
     DArray<T> dinv;
     double lmax[4], lmin[4];
@@ -370,7 +370,8 @@ struct AmgDev {
     std::vector<std::unique_ptr<DevLevel<T>>> L;
     DArray<double> cinv;
     int64_t nc = 0;
-    int degree = 2;
+    int degree = 2;                          // Chebyshev steps after the coarse-grid correction
+    int pre = 1;                             // and before it (the first from x = 0: no operator product)
     std::vector<std::vector<Coef4>> coef;   // per level: coefficients of each Chebyshev step
 };
 
@@ -452,8 +453,9 @@ static void level_vectors_and_coefs(AmgDev<T>& D, DevLevel<T>& L, int degree, cu
 }
 
 template <class T>
-static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, cudaStream_t st) {
+static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, int pre, cudaStream_t st) {
     D.degree = degree;
+    D.pre = pre;
     for (size_t l = 0; l < H.levels.size(); ++l) {
         const HostLevel& HL = H.levels[l];
         auto L = std::make_unique<DevLevel<T>>();
@@ -471,7 +473,7 @@ static void upload_hierarchy(AmgDev<T>& D, const HostHierarchy& H, int degree, c
             L->P.upload(HL.P, st);
             L->R.upload(HL.R, st);
         }
-        level_vectors_and_coefs(D, *L, degree, st);
+        level_vectors_and_coefs(D, *L, std::max(degree, pre), st);
         D.L.push_back(std::move(L));
     }
     D.nc = H.nc;
@@ -536,8 +538,9 @@ static bool take_sell(DevLevel<T>& L, DevCsr4d& A, cudaStream_t st) {
 // The same device hierarchy as upload_hierarchy, taken over from the GPU setup level by level
 // (each level's setup arrays are released as soon as its V-cycle copy exists)
 template <class T>
-static void take_hierarchy(AmgDev<T>& D, GpuHierarchy& H, int degree, cudaStream_t st) {
+static void take_hierarchy(AmgDev<T>& D, GpuHierarchy& H, int degree, int pre, cudaStream_t st) {
     D.degree = degree;
+    D.pre = pre;
     for (auto& G : H.levels) {
         auto L = std::make_unique<DevLevel<T>>();
         const int64_t n = G->A.n_rows;
@@ -554,14 +557,14 @@ static void take_hierarchy(AmgDev<T>& D, GpuHierarchy& H, int degree, cudaStream
             L->P.take(G->P, st);
             L->R.take(G->R, st);
         }
-        level_vectors_and_coefs(D, *L, degree, st);
+        level_vectors_and_coefs(D, *L, std::max(degree, pre), st);
         D.L.push_back(std::move(L));
     }
     D.nc = H.nc;
     D.cinv.upload(H.coarse_inv, st);
 }
 
-void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degree) {
+void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degree, int pre) {
     delete p->amg;
     p->amg = new AmgHierarchy();
     p->amg->precision = precision;
@@ -574,16 +577,16 @@ void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degre
     if (precision == KNP_PREC_FP32) {
         auto* D = new AmgDev<float>();
         p->amg->h32 = D;
-        upload_hierarchy(*D, H, degree, p->stream);
+        upload_hierarchy(*D, H, degree, pre, p->stream);
     } else {
         auto* D = new AmgDev<double>();
         p->amg->h64 = D;
-        upload_hierarchy(*D, H, degree, p->stream);
+        upload_hierarchy(*D, H, degree, pre, p->stream);
     }
     KNP_CUDA(cudaStreamSynchronize(p->stream));
 }
 
-void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree) {
+void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree, int pre) {
     delete p->amg;
     p->amg = new AmgHierarchy();
     p->amg->precision = precision;
@@ -599,11 +602,11 @@ void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree) {
     if (precision == KNP_PREC_FP32) {
         auto* D = new AmgDev<float>();
         p->amg->h32 = D;
-        take_hierarchy(*D, H, degree, p->stream);
+        take_hierarchy(*D, H, degree, pre, p->stream);
     } else {
         auto* D = new AmgDev<double>();
         p->amg->h64 = D;
-        take_hierarchy(*D, H, degree, p->stream);
+        take_hierarchy(*D, H, degree, pre, p->stream);
     }
     H.levels.clear();
     KNP_CUDA(cudaStreamSynchronize(p->stream));
@@ -680,7 +683,7 @@ static void vcycle_rec(AmgDev<T>& D, int l, const double* v, const double* s, co
         return;
     }
     DevLevel<T>& C = *D.L[l + 1];
-    smooth(L, D.coef[l], D.degree, true, v, s, df, pr, l == 0, st);
+    smooth(L, D.coef[l], D.pre, true, v, s, df, pr, l == 0, st);
     residual(L, pr, l == 0, st);
     csr_apply(L.R, L.r.p, C.b.p, 0, st);
     vcycle_rec(D, l + 1, nullptr, nullptr, DeflFuse{}, pr, st);
@@ -874,7 +877,7 @@ static void na_vcycle_rec(AmgDev<T>& D, std::vector<NaWork<T>>& W, int l, const 
     const std::vector<Coef4>& cs = D.coef[l];
     count_launch();
     k_cheb_first<T><<<nblk(L.n, 256), 256, 0, st>>>(L.n, v, s, w.b, L.dinv.p, cs[0], w.x, w.d, DeflFuse{});
-    for (int k = 1; k < D.degree; ++k) na_cheb_step(L, w, cs[k], st);
+    for (int k = 1; k < D.pre; ++k) na_cheb_step(L, w, cs[k], st);
     count_launch();
     if (L.sell) {
         k_resid_sell<T><<<nblk(L.n, 128), 128, 0, st>>>(L.n, L.sp.p, L.scol.p, L.sval.p, w.x, w.b, w.r);

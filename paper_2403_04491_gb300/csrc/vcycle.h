@@ -53,10 +53,11 @@ struct AmgHierarchy {
     ~AmgHierarchy();
 };
 
-void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degree);
+// degree / pre: Chebyshev steps after / before the coarse-grid correction on every level
+void amg_upload(knp_problem* p, const HostHierarchy& H, int precision, int degree, int pre);
 struct GpuHierarchy;
 // the hierarchy built by amg_build_gpu, taken over on the device (consumes H)
-void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree);
+void amg_take_gpu(knp_problem* p, GpuHierarchy& H, int precision, int degree, int pre);
 // z = V-cycle(s .* v); with df (y set), z = V-cycle(s .* v - A Z y) + Z y (the coarse correction's
 // passes fused into the first and last kernels)
 void vcycle_apply(knp_problem* p, const double* v, const double* s, double* z, const DeflFuse* df = nullptr);

@@ -69,7 +69,7 @@ class AmgOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("theta", C.c_double), ("coarse_max", C.c_int32),
                 ("max_levels", C.c_int32), ("cheb_degree", C.c_int32), ("cheb_ratio", C.c_double),
                 ("theta_coarse", C.c_double), ("p_drop", C.c_double), ("host_setup", C.c_int32),
-                ("inner_cg_max_it", C.c_int32), ("inner_cg_rtol", C.c_double)]
+                ("inner_cg_max_it", C.c_int32), ("inner_cg_rtol", C.c_double), ("cheb_degree_pre", C.c_int32)]
 
 
 class AmgSetupRecord(C.Structure):
@@ -349,11 +349,12 @@ class Problem:
 
     def amg_setup(self, precision=KNP_PREC_FP64, theta=0.08, coarse_max=500, max_levels=12, cheb_degree=2,
                   cheb_ratio=3.0, theta_coarse=0.0, p_drop=0.0, host_setup=False, inner_cg_max_it=0,
-                  inner_cg_rtol=1e-8):
+                  inner_cg_rtol=1e-8, cheb_degree_pre=1):
         """inner_cg_max_it > 0 selects CG(P_0) (V-cycle-preconditioned CG per field block of P_0,
-        to inner_cg_rtol) instead of one V-cycle."""
+        to inner_cg_rtol) instead of one V-cycle. cheb_degree / cheb_degree_pre: Chebyshev steps
+        after / before the coarse-grid correction."""
         o = AmgOpts(precision, theta, coarse_max, max_levels, cheb_degree, cheb_ratio, theta_coarse, p_drop,
-                    int(host_setup), int(inner_cg_max_it), float(inner_cg_rtol))
+                    int(host_setup), int(inner_cg_max_it), float(inner_cg_rtol), int(cheb_degree_pre))
         _check(_lib.knp_amg_setup(self.handle, C.byref(o)))
 
     def solve(self, rtol=1e-10, restart=30, max_it=1000, phi_e_group=False, deflate=True, stop_test=KNP_TEST_SCALED,
