@@ -384,13 +384,23 @@ AmgHierarchy::~AmgHierarchy() {
 }
 
 // A level's operator is stored sliced-ELL (one thread per row, the value loads of a warp
-// contiguous) unless padding every slice to its longest row would store more than this many
-// entries per nonzero; then CSR with a few lanes per row. Measured on the 512-cell 256^3
-// workload, whose first coarse level has 58 entries per row: sliced ELL there (and on the
-// second, 39 per row) is 2.4% faster per FGMRES iteration than CSR.
+// contiguous) if its rows are short (at most SELL_SHORT_ROW entries on average), or if they are
+// long but there are enough of them to keep the GPU busy with one thread each (at least
+// SELL_MIN_LONG_ROWS); and in either case only if padding every slice to its longest row stores
+// at most SELL_MAX_STORED entries per nonzero. Otherwise CSR with 4 S lanes per row. Measured:
+// the 512-cell 256^3 workload's first coarse level (1.7M rows of 58 entries) is 2.4% faster per
+// FGMRES iteration as sliced ELL; P2's first coarse level at 32^3 (19.5k rows of 143 entries, four
+// warps per SM with one thread per row) made the step 1.8 times slower.
 constexpr double SELL_MAX_STORED = 2.0;
+constexpr double SELL_SHORT_ROW = 24.0;
+constexpr int64_t SELL_MIN_LONG_ROWS = 152 * 1024;
 
-// sliced ELL of a host CSR level; false (nothing done) if the padding exceeds SELL_MAX_STORED
+static bool sell_suits(int64_t rows, int64_t nnz) {
+    return (double)nnz <= SELL_SHORT_ROW * (double)std::max<int64_t>(rows, 1) || rows >= SELL_MIN_LONG_ROWS;
+}
+
+// sliced ELL of a host CSR level; false (nothing done) if the level does not suit it (sell_suits,
+// SELL_MAX_STORED)
 template <class T>
 static bool upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
     const int64_t n = A.n_rows;
@@ -401,7 +411,8 @@ static bool upload_sell(DevLevel<T>& L, const HostCsr4& A, cudaStream_t st) {
         for (int64_t r = s * SELL_C; r < std::min(n, (s + 1) * SELL_C); ++r) w = std::max(w, A.ptr[r + 1] - A.ptr[r]);
         sp[s + 1] = sp[s] + w * SELL_C;
     }
-    if ((double)sp[ns] > SELL_MAX_STORED * (double)std::max<int64_t>(A.nnz(), 1)) return false;
+    if (!sell_suits(n, A.nnz()) || (double)sp[ns] > SELL_MAX_STORED * (double)std::max<int64_t>(A.nnz(), 1))
+        return false;
     std::vector<int32_t> col(sp[ns]);
     std::vector<T> val(4 * sp[ns], T(0));
     for (int64_t s = 0; s < ns; ++s) {
@@ -512,11 +523,12 @@ __global__ void k_sell_fill(int64_t n, int64_t ns, const int64_t* __restrict__ p
     }
 }
 
-// sliced ELL of a device CSR level (its CSR arrays released); false (nothing done) if the padding
-// exceeds SELL_MAX_STORED
+// sliced ELL of a device CSR level (its CSR arrays released); false (nothing done) if the level
+// does not suit it (sell_suits, SELL_MAX_STORED)
 template <class T>
 static bool take_sell(DevLevel<T>& L, DevCsr4d& A, cudaStream_t st) {
     const int64_t n = A.n_rows, ns = (n + SELL_C - 1) / SELL_C;
+    if (!sell_suits(n, A.nnz)) return false;
     DArray<int64_t> w;
     w.alloc(std::max<int64_t>(ns, 1));
     k_sell_widths<<<nblk(ns, 256), 256, 0, st>>>(n, ns, A.ptr.p, w.p);
