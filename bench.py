@@ -585,7 +585,15 @@ def adjoint_bench(args):
     m = cfg.mesh
     ni, ne = mesh.nodes()
     idx, w = probe_weights(m.coords, m.elems, m.elem_tag, ne, prob.N_i, prob.N_e, probe_points(cfg))
-    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=rtol, max_it=4000 if cfg.mixed else 1000)
+    max_it = 4000 if cfg.mixed else 1000
+    sim = Simulation(prob, idx, w, n_steps, checkpoint_every=20, rtol=rtol, max_it=max_it)
+    # warm-up: a short forward and reverse sweep from the same initial state, so that the timed run
+    # does not pay the first use of each kernel, graph and work array (the first forward of a
+    # fresh process took 3.8 s more than the same forward repeated, on the 200-step 2D workload)
+    warm = Simulation(prob, idx, w, max(1, args.warmup), checkpoint_every=20, rtol=rtol, max_it=max_it)
+    gKw = torch.tensor(prob._facet_gleak[:, 1].copy(), requires_grad=True)
+    cKw = torch.tensor(warm.s0["c_i"][1].copy(), requires_grad=True)
+    (KNPFunction.apply(gKw, cKw, warm) ** 2).sum().backward()
     gK = torch.tensor(prob._facet_gleak[:, 1].copy(), requires_grad=True)
     cK = torch.tensor(sim.s0["c_i"][1].copy(), requires_grad=True)
     torch.cuda.synchronize()
@@ -601,7 +609,8 @@ def adjoint_bench(args):
                 config=dict(workload=workload_name(cfg, prob.n_dof) + f", {n_steps} steps, checkpoint every 20, "
                             "loss = sum of phi_e^2 at 64 probes", n_dof=prob.n_dof, rtol=rtol,
                             precision="fp32" if cfg.mixed else "fp64"),
-                setup_s=t_setup, device_memory_gb=device_memory_gb(torch), host_peak_rss_gb=host_peak_rss_gb(),
+                setup_s=t_setup, warmup_steps=max(1, args.warmup), device_memory_gb=device_memory_gb(torch),
+                host_peak_rss_gb=host_peak_rss_gb(),
                 forward=dict(seconds=t1 - t0, value=prob.n_dof * n_steps / (t1 - t0)),
                 adjoint=dict(seconds=t2 - t1, value=prob.n_dof * n_steps / (t2 - t1),
                              note="includes recomputing every segment from its checkpoint"),
