@@ -7,9 +7,10 @@
 //
 // The eight CGs run in lockstep on the interleaved [node][4] vectors; each has its own step
 // lengths and its own stopping test ||r_g|| <= rtol ||b_g||. A block that has converged keeps
-// its iterate (step lengths 0). P_0 and the V-cycle are symmetric positive definite (the
-// V-cycle smooths with the same Chebyshev polynomial before and after and solves the coarsest
-// level exactly), as CG needs. The dot products come to the host once per inner iteration.
+// its iterate (step lengths 0). P_0 and the V-cycle are symmetric positive definite (for CG(P_0)
+// knp_amg_setup gives the V-cycle the same Chebyshev steps before and after, and the coarsest
+// level is solved exactly), as CG needs. The dot products come to the host once per inner
+// iteration.
 #include <cmath>
 #include <vector>
 

@@ -4,12 +4,18 @@
 // storage/arithmetic type of the hierarchy: double (plain FP64 form) or float (the
 // mixed-precision form; the coarsest dense solve is FP64 in both).
 //
-// Layouts: the finest operator (about 15 entries per row in 3D) is sliced-ELL with one
-// thread per row; coarser operators and the transfer operators are CSR processed by
-// groups of 4 x S threads per row, one thread per (field, entry slot): each thread does one
-// multiply-add per entry and the group reduces one value per field over its S slots (S a
-// power of two chosen from the mean row length), so that the short, wide coarse levels
-// still fill the GPU without spending the slow FP64 pipe on four-value reductions.
+// Layouts: a level operator with short rows (the finest, about 15 entries per row in 3D) or
+// with enough rows to fill the GPU one thread per row is sliced-ELL with one thread per row;
+// the other operators and the transfer operators are CSR processed by groups of 4 x S threads
+// per row, one thread per (field, entry slot): each thread does one multiply-add per entry and
+// the group reduces one value per field over its S slots (S a power of two chosen from the mean
+// row length), so that the short, wide coarse levels still fill the GPU without spending the
+// slow FP64 pipe on four-value reductions.
+//
+// Smoothing: Chebyshev steps on [lambda_max / ratio, 1.1 lambda_max] per field, `pre` of them
+// before the coarse-grid correction (the first from x = 0 costs no operator product) and
+// `degree` after; one before and two after by default, which makes the V-cycle non-symmetric
+// (FGMRES takes any preconditioner; CG(P_0) is given as many steps before as after).
 #include <cmath>
 #include <cstdlib>
 #include <map>
