@@ -1,4 +1,4 @@
-// Adjoint of one time step (spec addition; the paper has no adjoint).
+// Adjoint of one time step (an addition to the method: the paper has no adjoint).
 //
 // For step n the equations are A_{n-1} u_n = f_n with A_{n-1}, f_n built from (u_{n-1}, w_n,
 // g_leak) and w_n = G(w_{n-1}, phi_M(u_{n-1})) (Rush-Larsen, Section 3.2). With
